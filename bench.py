@@ -1,0 +1,331 @@
+"""Benchmark of the batched C2C FFT on one B300 (or N, one rank per GPU).
+
+Workload (default, "sweep"): the power-of-two sweep N = 2^10 .. 2^24, each
+size holding 2^26 complex64 elements (512 MiB per buffer; batch 2^26/N),
+inputs i.i.d. normal(0,1) re-seeded per size with seed 1; one step = forward
+then inverse of every size.  Metric: GFLOP/s with the nominal 5*N*log2(N)
+flops per transform and direction.  Inputs are larger than L2 (126 MB), so
+no flush is needed between iterations.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the slow reference arm), on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1203_4938_b300 import inputs  # noqa: E402
+
+TOTAL_LOG2 = 26
+LO, HI = 10, 24
+METRIC = "C2C FFT GFLOP/s (5N*log2N/t), fwd+inv sweep N=2^10..2^24, 2^26 complex64 per size"
+
+
+def flops_per_step(lo=LO, hi=HI, total_log2=TOTAL_LOG2):
+    # per size and direction: batch * 5 N log2 N = 5 * 2^total * log2 N
+    return sum(2 * 5.0 * (1 << total_log2) * k for k in range(lo, hi + 1))
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        loaded = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle arm (bounded sample)
+# --------------------------------------------------------------------------
+def oracle_sample(budget_elems: int = 1 << 21, sizes=None):
+    """Time the FP64 oracle (forward + inverse) on min(batch, budget/N) transforms
+    of each sweep size; returns (GFLOP/s, seconds, threads, description)."""
+    import oracle
+    threads = oracle.num_cpus()
+    sizes = sizes or inputs.sweep_sizes(TOTAL_LOG2, LO, HI)
+    fl, secs = 0.0, 0.0
+    for k, n, b in sizes:
+        m = max(1, min(b, budget_elems // n))
+        x = inputs.normal_batch(m, n, seed=1)
+        t0 = time.perf_counter()
+        y = oracle.fft(x, -1, threads)
+        oracle.fft(y, +1, threads)
+        secs += time.perf_counter() - t0
+        fl += 2 * 5.0 * n * k * m
+    desc = (f"FP64 C oracle (radix-2), fwd+inv of min(batch, 2^21/N) transforms per size "
+            f"N=2^{LO}..2^{HI}, {threads} threads")
+    return fl / secs / 1e9, secs, threads, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    for _ in range(args.warmup if args.warmup else 0):
+        pass
+    vals, secs_total = [], 0.0
+    gf = None
+    for _ in range(max(1, args.steps)):
+        gf, secs, threads, desc = oracle_sample(1 << 19 if args.quick else 1 << 21)
+        vals.append(gf)
+        secs_total += secs
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs_total / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "sweep 2^10..2^24 x 2^26 elems (bounded CPU sample)"},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    from paper_1203_4938_b300 import build as B
+    from paper_1203_4938_b300 import fft as F
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    F.load()
+    stream = torch.cuda.current_stream(dev)
+    sizes = inputs.sweep_sizes(TOTAL_LOG2, args.lo, args.hi)
+    if args.quick:
+        sizes = [(k, n, max(1, b // 16)) for k, n, b in sizes]
+
+    # inputs resident in HBM; one output and one scratch buffer shared by all sizes
+    plans, xs = [], []
+    for k, n, b in sizes:
+        x = inputs.sweep_input(k, TOTAL_LOG2, seed=1)[:b]
+        xs.append(torch.from_numpy(x).to(dev))
+        plans.append(F.Plan((n,), b))
+    maxel = max(n * b for _, n, b in sizes)
+    y = torch.empty(maxel, dtype=torch.complex64, device=dev)
+    z = torch.empty(maxel, dtype=torch.complex64, device=dev)
+
+    launches = []  # (size index, direction, kernel index)
+    for i, p in enumerate(plans):
+        for d in (-1, +1):
+            for kk in range(p.kernel_count):
+                launches.append((i, d, kk))
+
+    def step(events=None):
+        j = 0
+        for i, p in enumerate(plans):
+            n, b = sizes[i][1], sizes[i][2]
+            yy, zz = y[:n * b].view(b, n), z[:n * b].view(b, n)
+            for d, src, dst in ((-1, xs[i], yy), (+1, yy, zz)):
+                for kk in range(p.kernel_count):
+                    if events is not None:
+                        events[j][0].record(stream)
+                    p.exec_kernel(kk, src, dst, d)
+                    if events is not None:
+                        events[j][1].record(stream)
+                    j += 1
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in launches] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # per-kernel durations inside the timed region
+    per = {}
+    for s in range(args.steps):
+        for j, (i, d, kk) in enumerate(launches):
+            dt = ev[s][j][0].elapsed_time(ev[s][j][1])
+            per.setdefault((i, kk), []).append(dt)
+    tot = {key: sum(v) for key, v in per.items()}
+    dom = max(tot, key=tot.get)
+    di, dk = dom
+    dn, db = sizes[di][1], sizes[di][2]
+    avg_ms = statistics.mean(per[dom])
+    alg_bytes = 16.0 * dn * db  # each kernel reads and writes every element once
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    share = tot[dom] / sum(tot.values())
+
+    fl = sum(2 * 5.0 * n * b * k for k, n, b in sizes)
+    value = world * fl / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host input -> device, fwd+inv, result -> host
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.empty(xs[i].shape, dtype=torch.complex64, pin_memory=True) for i in range(len(sizes))]
+        for i in range(len(sizes)):
+            hin[i].copy_(xs[i].cpu())
+        hout = torch.empty(maxel, dtype=torch.complex64, pin_memory=True)
+        xin = torch.empty(maxel, dtype=torch.complex64, device=dev)
+
+        def e2e_step():
+            for i, p in enumerate(plans):
+                n, b = sizes[i][1], sizes[i][2]
+                xi, yy, zz = xin[:n * b].view(b, n), y[:n * b].view(b, n), z[:n * b].view(b, n)
+                xi.copy_(hin[i], non_blocking=True)
+                p.exec(xi, yy, -1)
+                p.exec(yy, zz, +1)
+                hout[:n * b].view(b, n).copy_(zz, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1) / args.steps
+        bytes_io = sum(8 * n * b for _, n, b in sizes)
+        e2e = {"value": world * fl / (ems * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        gf, secs, threads, desc = oracle_sample(1 << 19 if args.quick else 1 << 21)
+        cpu = {"value": gf, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    if rank == 0:
+        kname = (f"k_cols_pow2 N1=2^{plans[di].describe()}" if False else plans[di].describe())
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sweep N=2^{args.lo}..2^{args.hi}, 2^{TOTAL_LOG2} complex64/size"
+                                   f"{' (quick: 1/16 batch)' if args.quick else ''}, fwd+inv, normal(0,1) seed 1",
+                       "l2": "inputs (512 MiB per size) larger than L2; no flush", "parallelism": f"replicas{world}"},
+            "gpu_launches": args.steps * len(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"size N=2^{int(math.log2(dn))} kernel #{dk} of [{kname}]",
+                         "kernel_time_share": share, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
+                         if "hbm_gbs" in peaks else "fallback 6.4 TB/s"},
+            "clocks": clocks,
+            "per_size_ms": {f"2^{sizes[i][0]}": sum(statistics.mean(per[(i, kk)]) for kk in
+                                                   range(plans[i].kernel_count)) * 2 for i in range(len(sizes))},
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lo", type=int, default=LO)
+    ap.add_argument("--hi", type=int, default=HI)
+    ap.add_argument("--quick", action="store_true", help="1/16 of the batch (smoke runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

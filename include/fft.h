@@ -1,0 +1,138 @@
+/*
+ * fft.h -- C ABI of the B300 batched complex-to-complex FFT library
+ * (libb300fft.so, sm_103a).
+ *
+ * The operation is the discrete Fourier transform of the paper's Sec. III-A
+ * example ("Discrete Fourier Transform Example"): for every length-N sequence
+ * x of a batch,
+ *
+ *     X[k] = sum_{n<N} x[n] * exp(-2*pi*i*n*k/N)     (FFT_FORWARD)
+ *     X[k] = sum_{n<N} x[n] * exp(+2*pi*i*n*k/N)     (FFT_INVERSE)
+ *
+ * unnormalised in both directions, output in natural order.  The paper builds
+ * the DFT of N = N1*N2 points from DFTs of sizes N1 and N2 (Cooley-Tukey) and
+ * ships a flow of many small DFTs to the data-parallel device; here every
+ * level runs on the GPU.  The 2-D form (dims = 2, lengths = {H, W}) is the
+ * separable transform X[k1,k2] = sum x[n1,n2] W_H^(n1*k1) W_W^(n2*k2) over
+ * image-shaped data, the shape of the paper's Sec. III-B image example.
+ *
+ * Element type: complex64 = interleaved float pairs (re, im) -- the paper's
+ * float2 -- for input and output at every precision setting.
+ *
+ * Layouts:
+ *   1-D     [batch][N], contiguous.
+ *   2-D     [batch][H][W], row-major, contiguous.
+ *   ragged  the transforms are packed back to back; transform t starts at
+ *           element offset sum_{u<t} lengths[u].
+ *
+ * Ownership: the caller owns the input and output device buffers and the CUDA
+ * stream.  A plan owns its twiddle/chirp tables, its workspace, any captured
+ * CUDA graph and a device status word; fft_plan_destroy frees them.
+ * fft_exec allocates nothing and does not synchronise.
+ *
+ * Errors: argument errors are returned synchronously as fft_status values.
+ * Errors found by a kernel (e.g. a bounded wait that ran out) are written to
+ * the plan's device status word and returned by fft_plan_check after the
+ * caller has synchronised the stream.  No kernel traps.
+ *
+ * Threads: plans may be created and destroyed from any thread; one plan must
+ * not be executed concurrently on two streams when it uses a workspace
+ * (fft_plan_workspace_bytes > 0).
+ */
+#ifndef B300_FFT_H
+#define B300_FFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FFT_API __attribute__((visibility("default")))
+#else
+#define FFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_plan_s *fft_plan;
+
+typedef enum {
+    FFT_OK = 0,
+    FFT_ERR_INVALID_ARG = 1,  /* bad dims, length, batch, direction or NULL pointer */
+    FFT_ERR_UNSUPPORTED = 2,  /* valid request this library does not implement      */
+    FFT_ERR_ALLOC = 3,        /* device or host allocation failed at plan time       */
+    FFT_ERR_MISALIGNED = 4,   /* input or output pointer not 16-byte aligned         */
+    FFT_ERR_CUDA = 5,         /* a CUDA runtime call failed                          */
+    FFT_ERR_TIMEOUT = 6,      /* a bounded device-side wait expired                  */
+    FFT_ERR_BAD_HANDLE = 7    /* NULL, destroyed or foreign plan handle              */
+} fft_status;
+
+/* Arithmetic of the transform; input and output are complex64 in every mode. */
+typedef enum {
+    FFT_FP32 = 0,          /* FP32 Stockham passes on the CUDA cores             */
+    FFT_TC_FP16 = 1,       /* radix-16 stages as FP16 tensor-core GEMMs, hi+lo   */
+    FFT_TC_BF16 = 2,       /* radix-16 stages as BF16 tensor-core GEMMs, hi+lo   */
+    FFT_TC_FP16_PLAIN = 3, /* FP16 tensor-core stages without the lo correction  */
+    FFT_TC_BF16_PLAIN = 4  /* BF16 tensor-core stages without the lo correction  */
+} fft_precision;
+
+enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
+
+/* Create a plan for `batch` transforms of the given shape.
+ *   dims     1 or 2.
+ *   lengths  dims entries: {N} or {H, W}; every entry >= 1.
+ *   batch    number of transforms (>= 1).
+ *   precision one of fft_precision (tensor-core modes: 1-D, N = 16^k, k >= 2).
+ * Computes the twiddle tables on the device in FP64 and rounds them once to
+ * FP32; allocates the workspace a multi-pass length needs.  Synchronises the
+ * current device once.  Returns NULL on error; fft_last_error() says why. */
+FFT_API fft_plan fft_plan_create(int dims, const int64_t *lengths, int64_t batch, int precision);
+
+/* Create a plan for `count` 1-D transforms of uneven lengths, packed back to
+ * back (see Layouts).  lengths: host array of `count` entries, each in
+ * [1, 2^20].  The whole batch runs as one persistent kernel launch, captured
+ * once into a CUDA graph at plan time.  precision must be FFT_FP32. */
+FFT_API fft_plan fft_plan_create_ragged(const int64_t *lengths, int64_t count, int precision);
+
+/* Status of the last fft_plan_create* call on this host thread. */
+FFT_API fft_status fft_last_error(void);
+
+/* Enqueue the transform of `in` into `out` on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  in and out are device pointers,
+ * 16-byte aligned, holding the plan's elements; in == out is allowed.
+ * direction: FFT_FORWARD or FFT_INVERSE.  Asynchronous; allocates nothing. */
+FFT_API fft_status fft_exec(fft_plan plan, const void *in, void *out, int direction, void *stream);
+
+/* Read and clear the plan's device status word (synchronous; call it after
+ * the stream that ran fft_exec has been synchronised). */
+FFT_API fft_status fft_plan_check(fft_plan plan);
+
+/* Free every resource of the plan.  Synchronises the device first. */
+FFT_API fft_status fft_plan_destroy(fft_plan plan);
+
+/* Bytes of device workspace the plan holds (0 for single-pass plans). */
+FFT_API size_t fft_plan_workspace_bytes(fft_plan plan);
+
+/* Static English text for a status value. */
+FFT_API const char *fft_status_string(fft_status status);
+
+/* Number of kernel launches one fft_exec of this plan enqueues (a captured
+ * graph counts its kernels).  0 for an invalid handle. */
+FFT_API int fft_plan_kernel_count(fft_plan plan);
+
+/* Enqueue only kernel `k` (0 <= k < fft_plan_kernel_count) of the sequence
+ * fft_exec would enqueue, with the same arguments; intermediate results live
+ * in the plan's workspace, so running k = 0, 1, ... in order on one stream is
+ * exactly fft_exec.  For per-kernel timing and profiling. */
+FFT_API fft_status fft_exec_kernel(fft_plan plan, int k, const void *in, void *out, int direction, void *stream);
+
+/* Human-readable one-line description of the plan's decomposition (kernel
+ * family, radix sequence, tile shape) copied into buf (NUL-terminated,
+ * truncated to cap bytes).  Returns the full length, or -1 on a bad handle. */
+FFT_API int fft_plan_describe(fft_plan plan, char *buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* B300_FFT_H */

@@ -5,7 +5,7 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 and never imports it.  The arithmetic lives in ``oracle.c`` (plain C, FP64);
 this module compiles it with gcc on first use and marshals numpy arrays.
 
-Definition followed (paper Sec. IV-A, the DFT example): for a length-N complex
+Definition followed (paper Sec. III-A, the DFT example): for a length-N complex
 sequence, ``X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N)`` with sign -1 for the
 forward and +1 for the inverse transform, both unnormalised; the paper
 computes it with radix-2 Cooley-Tukey, which ``fft`` follows for powers of two.

@@ -6,7 +6,7 @@
  * the CUDA library.  Only the test-suite, the smoke check and the timed CPU
  * baseline of the benchmark load it.
  *
- * What is computed (paper Sec. IV-A, "Discrete Fourier Transform Example"):
+ * What is computed (paper Sec. III-A, "Discrete Fourier Transform Example"):
  * the DFT of a length-N complex sequence,
  *
  *     X[k] = sum_{n<N} x[n] * exp(sign * 2*pi*i * n*k / N),   sign = -1 forward,

@@ -1,0 +1,72 @@
+// plan.h -- the plan object behind the opaque fft_plan handle.  Internal.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fft.h"
+
+namespace b300fft {
+
+constexpr uint64_t kPlanMagic = 0xB300FF7A5EEDULL;
+
+enum class PlanKind : int {
+    None = 0,
+    Rows,      // single-pass power-of-two rows kernel
+    FourStep,  // columns + transposed rows, through the workspace
+    TwoD,      // rows pass then in-place columns pass
+    Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
+    Bluestein, // chirp-z through a power-of-two convolution
+    Ragged,    // persistent work-queue kernel over uneven lengths
+    TensorCore // radix-16 stages as tensor-core GEMMs
+};
+
+struct GenericPlan;   // generic.cu
+struct RaggedPlan;    // ragged.cu
+struct TcPlan;        // tc.cu
+
+}  // namespace b300fft
+
+struct fft_plan_s {
+    uint64_t magic = 0;
+    int dims = 1;
+    int64_t len[2] = {1, 1};
+    int64_t batch = 1;
+    int64_t elements = 0;  // complex elements per exec (in and out)
+    int precision = 0;
+    b300fft::PlanKind kind = b300fft::PlanKind::None;
+    int single_max_log = 12;  // largest power-of-two length done in one pass
+
+    // power-of-two kernels
+    int logn_a = 0, logn_b = 0, sh = 0;
+    int cols_c = 0;  // columns kernel width
+    size_t off_a = 0, off_b = 0, off_lo = 0, off_hi = 0;  // into d_tables (float2 units)
+
+    float2* d_tables = nullptr;
+    float2* d_work = nullptr;
+    size_t work_bytes = 0;
+    int* d_status = nullptr;
+    void* d_aux = nullptr;  // kind-specific device block (descriptors, queues)
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+
+    b300fft::GenericPlan* generic = nullptr;
+    b300fft::RaggedPlan* ragged = nullptr;
+    b300fft::TcPlan* tc = nullptr;
+
+    int kernels = 0;
+    char desc[256] = {0};
+};
+
+namespace b300fft {
+
+void destroy_plan_resources(fft_plan_s* p);
+// only < 0: every kernel; else only kernel `only` of the sequence
+fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only = -1);
+
+// Builders of the other kernel families (return FFT_ERR_UNSUPPORTED when the
+// shape is outside what they implement).
+fft_status build_generic_1d(fft_plan_s* p);
+fft_status build_tc_plan(fft_plan_s* p);
+
+}  // namespace b300fft

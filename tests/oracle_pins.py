@@ -9,7 +9,7 @@ O(N^2) definition, and an independent library witness (``torch.fft`` in
 complex128 on the CPU).  The same pins are run against copies of the oracle
 with planted mistakes to show that each kind of mistake is caught.
 
-Definition pinned (paper Sec. IV-A): X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N),
+Definition pinned (paper Sec. III-A): X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N),
 sign -1 forward, +1 inverse, unnormalised.
 """
 from __future__ import annotations

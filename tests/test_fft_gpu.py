@@ -1,0 +1,164 @@
+"""Parity of the FP32 CUDA path with the FP64 oracle (needs a GPU).
+
+Each case runs the kernels through the C ABI on seeded synthetic input and
+compares every transform with the oracle: the bar is a per-transform
+relative L2 error <= 1e-6 (max over the batch), in FP64."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_4938_b300 import inputs
+from tests.gpu_util import TOL_FP32, cuda_or_skip, max_rel_l2, run, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+# ---------------------------------------------------------------- 1-D pow2
+@pytest.mark.parametrize("logn", list(range(0, 15)))
+@pytest.mark.parametrize("batch", [1, 7, 37])
+def test_rows_single_pass(torch, logn, batch):
+    n = 1 << logn
+    x = inputs.uniform_batch(batch, n, seed=logn * 100 + batch)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d)
+        ref = oracle.fft(x, d)
+        assert max_rel_l2(y, ref, -1) <= TOL_FP32, (n, batch, d)
+
+
+@pytest.mark.parametrize("logn", [13, 14, 15, 16, 17, 18, 19, 20])
+def test_fourstep(torch, logn):
+    n = 1 << logn
+    batch = 3 if logn <= 18 else 2
+    x = inputs.normal_batch(batch, n, seed=logn)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d)
+        ref = oracle.fft(x, d)
+        assert max_rel_l2(y, ref, -1) <= TOL_FP32, (n, d)
+
+
+@pytest.mark.parametrize("logn", [21, 22, 23, 24])
+def test_fourstep_large(torch, logn):
+    n = 1 << logn
+    x = inputs.normal_batch(1, n, seed=logn)
+    y = run((n,), 1, x, -1)
+    ref = oracle.fft(x, -1)
+    assert max_rel_l2(y, ref, -1) <= TOL_FP32
+
+
+def test_config_small_uniform_1024x64(torch):
+    """N=1024, batch 64, uniform[-1,1] from seed 0, forward."""
+    x = inputs.uniform_batch(64, 1024, seed=0)
+    y = run((1024,), 64, x, -1)
+    err = max_rel_l2(y, oracle.fft(x, -1), -1)
+    assert err <= TOL_FP32, err
+
+
+@pytest.mark.parametrize("logn", [4, 10, 12, 16, 20])
+def test_round_trip(torch, logn):
+    n = 1 << logn
+    x = inputs.normal_batch(2, n, seed=7)
+    y = run((n,), 2, run((n,), 2, x, -1), +1) / n
+    assert max_rel_l2(y, x, -1) <= 2 * TOL_FP32
+
+
+@pytest.mark.parametrize("logn", [6, 12, 18])
+def test_in_place(torch, logn):
+    n = 1 << logn
+    x = inputs.uniform_batch(5, n, seed=11)
+    y = run((n,), 5, x, -1, inplace=True)
+    assert max_rel_l2(y, oracle.fft(x, -1), -1) <= TOL_FP32
+
+
+def test_impulse_exact_ones(torch):
+    """delta -> all ones: every butterfly only adds zeros, so FP32 is exact."""
+    for logn in (3, 8, 12, 16):
+        n = 1 << logn
+        x = np.zeros((2, n), np.complex64)
+        x[:, 0] = 1
+        y = run((n,), 2, x, -1)
+        assert np.array_equal(y, np.ones_like(y)), n
+
+
+def test_large_batch_tiny_n(torch):
+    x = inputs.uniform_batch(1 << 18, 2, seed=5)
+    y = run((2,), 1 << 18, x, -1)
+    assert max_rel_l2(y, oracle.fft(x, -1), -1) <= TOL_FP32
+
+
+# ---------------------------------------------------------------- 2-D
+@pytest.mark.parametrize("h,w,b", [(2, 2, 1), (16, 64, 3), (64, 16, 2), (256, 512, 2), (1024, 1024, 1),
+                                   (4096, 64, 1), (32, 8192, 1)])
+def test_2d(torch, h, w, b):
+    rng = np.random.default_rng(h * 7 + w)
+    x = inputs.image_batch(rng, b, h, w)
+    for d in (-1, +1):
+        y = run((h, w), b, x, d)
+        ref = oracle.fft2(x, d)
+        assert max_rel_l2(y.reshape(b, -1), ref.reshape(b, -1), -1) <= TOL_FP32, (h, w, d)
+
+
+# ---------------------------------------------------------------- ABI on GPU
+def test_misaligned_pointer(torch):
+    from paper_1203_4938_b300 import fft as F
+    with F.Plan((64,), 4) as p:
+        buf = torch.zeros(64 * 4 + 2, dtype=torch.complex64, device="cuda")
+        base = buf.data_ptr()
+        assert F.fft_exec(p.handle, base + 8, base, F.FFT_FORWARD) == F.FFT_ERR_MISALIGNED
+        assert F.fft_exec(p.handle, base, base + 8, F.FFT_FORWARD) == F.FFT_ERR_MISALIGNED
+        assert F.fft_exec(p.handle, base, base, 0) == F.FFT_ERR_INVALID_ARG
+        assert F.fft_exec(p.handle, 0, base, F.FFT_FORWARD) == F.FFT_ERR_INVALID_ARG
+
+
+def test_exec_after_destroy(torch):
+    from paper_1203_4938_b300 import fft as F
+    h = F.fft_plan_create(1, [256], 2, 0)
+    assert h
+    assert F.fft_plan_destroy(h) == F.FFT_OK
+    buf = torch.zeros(512, dtype=torch.complex64, device="cuda")
+    assert F.fft_exec(h, buf.data_ptr(), buf.data_ptr(), -1) == F.FFT_ERR_BAD_HANDLE
+    assert F.fft_plan_destroy(h) == F.FFT_ERR_BAD_HANDLE
+
+
+def test_workspace_and_description(torch):
+    from paper_1203_4938_b300 import fft as F
+    with F.Plan((4096,), 3) as p:
+        assert p.workspace_bytes == 0 and p.kernel_count == 1
+        assert "rows" in p.describe()
+    with F.Plan((1 << 16,), 3) as p:
+        assert p.workspace_bytes == (1 << 16) * 3 * 8 and p.kernel_count == 2
+        assert "fourstep" in p.describe()
+
+
+def test_side_stream_and_graph_capture(torch):
+    from paper_1203_4938_b300 import fft as F
+    n, b = 1 << 14, 4
+    x = inputs.uniform_batch(b, n, seed=3)
+    ref = oracle.fft(x, -1)
+    for shape in [(n,), (1 << 16,)]:
+        nn = shape[0]
+        xx = inputs.uniform_batch(b, nn, seed=4)
+        rr = oracle.fft(xx, -1)
+        with F.Plan(shape, b) as p:
+            d = to_dev(xx)
+            out = torch.empty_like(d)
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                p.exec(d, out)
+            torch.cuda.current_stream().wait_stream(s)
+            torch.cuda.synchronize()
+            assert max_rel_l2(out.cpu().numpy(), rr, -1) <= TOL_FP32
+            g = torch.cuda.CUDAGraph()
+            out2 = torch.empty_like(d)
+            with torch.cuda.graph(g):
+                p.exec(d, out2)
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            assert max_rel_l2(out2.cpu().numpy(), rr, -1) <= TOL_FP32
+    del ref
