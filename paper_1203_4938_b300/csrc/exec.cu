@@ -1,5 +1,6 @@
 // exec.cu -- fft_exec dispatch: enqueue the kernels of a plan on a stream.
 #include "launch.h"
+#include "persist.cuh"
 #include "plan.h"
 
 namespace b300fft {
@@ -9,7 +10,7 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
     auto want = [only](int k) { return only < 0 || only == k; };
     switch (p->kind) {
         case PlanKind::Rows:
-            if (want(0)) e = launch_rows(p->logn_a, inv, false, in, out, p->batch, p->d_tables + p->off_a, 1, st);
+            if (want(0)) e = launch_rows(p->logn_a, inv, in, out, p->batch, p->d_tables + p->off_a, st);
             break;
         case PlanKind::FourStep: {
             const int64_t n1 = int64_t(1) << p->logn_a, n2 = int64_t(1) << p->logn_b;
@@ -17,12 +18,38 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                 e = launch_cols(p->logn_a, p->cols_c, inv, true, in, p->d_work, n2, n2, n1 * n2, p->batch,
                                 p->d_tables + p->off_a, p->d_tables + p->off_lo, p->d_tables + p->off_hi, p->sh, st);
             if (e == cudaSuccess && want(1))
-                e = launch_rows(p->logn_b, inv, true, p->d_work, out, p->batch * n1, p->d_tables + p->off_b, n1, st);
+                e = launch_rowsT(p->logn_b, p->rowsT_tpc, inv, p->d_work, out, p->batch * n1, p->d_tables + p->off_b, n1,
+                                 st);
+            break;
+        }
+        case PlanKind::FourStepPersist: {
+            if (!want(0)) break;
+            PersistArgs a;
+            a.in = in;
+            a.out = out;
+            a.work = p->d_work;
+            a.ctl = static_cast<int*>(p->d_aux);
+            a.status = p->d_status;
+            a.batch = p->batch;
+            a.cb = p->pcb;
+            a.nch = p->pnch;
+            a.na = p->pna;
+            a.nb = p->pnb;
+            a.tw_a = p->d_tables + p->off_a;
+            a.tw_b = p->d_tables + p->off_b;
+            a.lo = p->d_tables + p->off_lo;
+            a.hi = p->d_tables + p->off_hi;
+            a.sh = p->sh;
+            a.spin_limit = p->spin_limit;
+            a.withhold_chunk = p->withhold_chunk;
+            e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch), st);
+            if (e == cudaSuccess)
+                e = launch_fourstep_persist(PersistConfig{p->pl1, p->pc, p->pl2, p->ptpc}, inv, a, p->pgrid, st);
             break;
         }
         case PlanKind::TwoD: {
             const int64_t h = p->len[0], w = p->len[1];
-            if (want(0)) e = launch_rows(p->logn_a, inv, false, in, out, p->batch * h, p->d_tables + p->off_a, 1, st);
+            if (want(0)) e = launch_rows(p->logn_a, inv, in, out, p->batch * h, p->d_tables + p->off_a, st);
             if (e == cudaSuccess && want(1))
                 e = launch_cols(p->logn_b, p->cols_c, inv, false, out, out, w, w, h * w, p->batch, p->d_tables + p->off_b,
                                 nullptr, nullptr, 0, st);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -16,6 +17,7 @@
 
 #include "../../include/fft.h"
 #include "launch.h"
+#include "persist.cuh"
 #include "plan.h"
 
 using namespace b300fft;
@@ -79,9 +81,81 @@ fft_status alloc_tables(fft_plan_s* p, size_t entries) {
     return FFT_OK;
 }
 
+int env_int(const char* name, int dflt) {
+    const char* v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+// Persistent four-step: both passes in one launch with L2-resident chunks.
+fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
+    // Measured best (l1, c, l2, tpc, chunk MiB) per log2 N on a B300 with 2^26
+    // elements per exec; 2^15 is faster as two launches, so it has no entry.
+    static const int kCfg[25][5] = {
+        {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
+        {8, 16, 8, 16, 16}, {8, 16, 9, 8, 16}, {8, 16, 10, 4, 16}, {9, 16, 10, 8, 16}, {10, 8, 10, 8, 16},
+        {11, 4, 10, 8, 16}, {11, 4, 11, 4, 48}, {12, 4, 11, 8, 16}, {12, 4, 12, 4, 48}};
+    const bool forced = std::getenv("B300FFT_PERSIST_CFG") != nullptr;
+    if (logn > 24 || (kCfg[logn][0] == 0 && !forced)) return FFT_ERR_UNSUPPORTED;
+    PersistConfig cfg{kCfg[logn][0], kCfg[logn][1], kCfg[logn][2], kCfg[logn][3]};
+    if (const char* v = std::getenv("B300FFT_PERSIST_CFG")) {
+        PersistConfig o{};
+        if (std::sscanf(v, "%d,%d,%d,%d", &o.l1, &o.c, &o.l2, &o.tpc) == 4 && o.l1 + o.l2 == logn) cfg = o;
+    }
+    if (!persist_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+    PersistInfo info;
+    if (persist_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n = int64_t(1) << logn, n1 = int64_t(1) << cfg.l1, n2 = int64_t(1) << cfg.l2;
+    const int64_t chunk_bytes = int64_t(env_int("B300FFT_CHUNK_MB", kCfg[logn][4] ? kCfg[logn][4] : 32)) << 20;
+    int64_t cb = chunk_bytes / (n * 8);
+    if (cb < 1) cb = 1;
+    if (cb > p->batch) cb = p->batch;
+    const int64_t nch = (p->batch + cb - 1) / cb;
+    const int64_t na = cb * (n2 / cfg.c), nb = cb * (n1 / cfg.tpc);
+    if (nch * (na + nb) > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+    p->kind = PlanKind::FourStepPersist;
+    p->pl1 = cfg.l1;
+    p->pc = cfg.c;
+    p->pl2 = cfg.l2;
+    p->ptpc = cfg.tpc;
+    p->pcb = cb;
+    p->pnch = (int)nch;
+    p->pna = (int)na;
+    p->pnb = (int)nb;
+    const int64_t items = nch * (na + nb);
+    const int64_t slots = (int64_t)sms * info.blocks_per_sm;
+    p->pgrid = (int)(items < slots ? items : slots);
+    p->spin_limit = env_int("B300FFT_SPIN_LIMIT", 1 << 23);
+    p->withhold_chunk = env_int("B300FFT_DEBUG_WITHHOLD_CHUNK", -1);
+    p->sh = (logn + 1) / 2;
+    const size_t ea = (size_t)pow2_table_entries(cfg.l1), eb = (size_t)pow2_table_entries(cfg.l2);
+    const size_t elo = size_t(1) << p->sh, ehi = size_t(1) << (logn - p->sh);
+    p->off_a = 0;
+    p->off_b = ea;
+    p->off_lo = ea + eb;
+    p->off_hi = p->off_lo + elo;
+    fft_status s = alloc_tables(p, p->off_hi + ehi);
+    if (s != FFT_OK) return s;
+    if (gen_pow2_table(p->d_tables + p->off_a, cfg.l1, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_pow2_table(p->d_tables + p->off_b, cfg.l2, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_lo, (int64_t)elo, 1, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_hi, (int64_t)ehi, (int64_t)elo, n, 0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    p->work_bytes = (size_t)n * (size_t)p->batch * sizeof(float2);
+    if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (cudaMalloc(&p->d_aux, sizeof(int) * (size_t)(1 + nch)) != cudaSuccess) return FFT_ERR_ALLOC;
+    p->kernels = 1;
+    std::snprintf(p->desc, sizeof p->desc,
+                  "fourstep-persist N=2^%d = 2^%d (C=%d) x 2^%d (tpc=%d) threads=%d grid=%d chunk=%lld x %lld",
+                  logn, cfg.l1, cfg.c, cfg.l2, cfg.tpc, info.threads, p->pgrid, (long long)cb, (long long)nch);
+    return FFT_OK;
+}
+
 fft_status build_pow2_1d(fft_plan_s* p, int logn) {
-    const int single_max = p->single_max_log;
-    if (logn <= single_max) {
+    p->single_max_log = env_int("B300FFT_SINGLE_MAX_LOG", p->single_max_log);
+    if (logn <= p->single_max_log && logn <= kRowsMaxLog) {
         p->kind = PlanKind::Rows;
         p->logn_a = logn;
         p->off_a = 0;
@@ -89,19 +163,39 @@ fft_status build_pow2_1d(fft_plan_s* p, int logn) {
         fft_status s = alloc_tables(p, ent);
         if (s != FFT_OK) return s;
         if (gen_pow2_table(p->d_tables + p->off_a, logn, 0) != cudaSuccess) return FFT_ERR_CUDA;
-        if (rows_prepare(logn, false) != cudaSuccess) return FFT_ERR_CUDA;
+        if (rows_prepare(logn) != cudaSuccess) return FFT_ERR_CUDA;
         p->kernels = 1;
-        std::snprintf(p->desc, sizeof p->desc, "rows N=2^%d tpc=%d threads=%d smem=%d", logn,
-                      rows_tpc(logn, false), rows_threads(logn, false), rows_smem(logn, false));
+        std::snprintf(p->desc, sizeof p->desc, "rows N=2^%d tpc=%d threads=%d", logn, rows_tpc(logn),
+                      rows_threads(logn));
         return FFT_OK;
+    }
+    if (env_int("B300FFT_PERSIST", 1)) {
+        fft_status ps = build_fourstep_persist(p, logn);
+        if (ps != FFT_ERR_UNSUPPORTED) return ps;
     }
     // four-step: N = N1 * N2, pass A = columns of length N1 (stride N2) with
     // the W_N^{n2 k1} twiddle, pass B = rows of length N2, transposed store.
-    int l2 = (logn + 1) / 2, l1 = logn - l2;
-    if (l2 > kColsMaxLog || l1 > kColsMaxLog || l2 < 5 || l1 < 1) return FFT_ERR_UNSUPPORTED;
-    if ((int64_t(1) << l2) % cols_width(l1) != 0) return FFT_ERR_UNSUPPORTED;
+    // Measured best (split log2 N1, column width, transposed rows per CTA)
+    // for each log2 N on a B300 with 2^26 elements per exec.
+    static const int kTuned[25][3] = {
+        {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0},
+        {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {7, 16, 32}, {7, 16, 32}, {7, 16, 8}, {8, 16, 8},
+        {8, 16, 8}, {8, 16, 8}, {8, 8, 4}, {9, 4, 4}, {10, 4, 4}, {11, 4, 4}, {12, 4, 4}, {12, 4, 4}};
+    const bool tuned = logn <= 24 && kTuned[logn][0] > 0;
+    int l1 = env_int("B300FFT_SPLIT_L1", tuned ? kTuned[logn][0] : logn / 2);
+    if (l1 < 1 || l1 >= logn) l1 = logn / 2;
+    const int l2 = logn - l1;
+    if (l2 > kColsMaxLog || l1 > kColsMaxLog || l2 < 5) return FFT_ERR_UNSUPPORTED;
+    const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+    int c = env_int("B300FFT_COLS_C", tuned ? kTuned[logn][1] : cols_width(l1));
+    if (!cols_width_valid(l1, c) || n2 % c != 0) c = cols_width_for(l1, n2);
+    if (c == 0) return FFT_ERR_UNSUPPORTED;
+    int tpc = env_int("B300FFT_ROWST_TPC", tuned ? kTuned[logn][2] : (c < 2 ? 2 : c));
+    while (tpc > 2 && (rowsT_threads(l2, tpc) > 1024 || n1 % tpc != 0)) tpc /= 2;
+    if (tpc < 2 || n1 % tpc != 0 || rowsT_threads(l2, tpc) > 1024) return FFT_ERR_UNSUPPORTED;
     p->kind = PlanKind::FourStep;
-    p->cols_c = cols_width(l1);
+    p->cols_c = c;
+    p->rowsT_tpc = tpc;
     p->logn_a = l1;
     p->logn_b = l2;
     p->sh = (logn + 1) / 2;
@@ -121,21 +215,23 @@ fft_status build_pow2_1d(fft_plan_s* p, int logn) {
         return FFT_ERR_CUDA;
     p->work_bytes = (size_t)n * (size_t)p->batch * sizeof(float2);
     if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
-    if (cols_prepare(l1, p->cols_c) != cudaSuccess || rows_prepare(l2, true) != cudaSuccess) return FFT_ERR_CUDA;
+    if (cols_prepare(l1, c) != cudaSuccess || rowsT_prepare(l2, tpc) != cudaSuccess) return FFT_ERR_CUDA;
     p->kernels = 2;
     std::snprintf(p->desc, sizeof p->desc,
-                  "fourstep N=2^%d = 2^%d (cols C=%d threads=%d) x 2^%d (rows-T tpc=%d threads=%d) work=%zuB",
-                  logn, l1, p->cols_c, cols_threads(l1, p->cols_c), l2, rows_tpc(l2, true), rows_threads(l2, true),
-                  p->work_bytes);
+                  "fourstep N=2^%d = 2^%d (cols C=%d threads=%d) x 2^%d (rowsT tpc=%d threads=%d) work=%zuB", logn,
+                  l1, c, cols_threads(l1, c), l2, tpc, rowsT_threads(l2, tpc), p->work_bytes);
     return FFT_OK;
 }
 
 fft_status build_pow2_2d(fft_plan_s* p, int logh, int logw) {
     if (logw > kRowsMaxLog || logh > kColsMaxLog || logh < 1) return FFT_ERR_UNSUPPORTED;
     p->kind = PlanKind::TwoD;
-    p->cols_c = cols_width_for(logh, int64_t(1) << logw);
     p->logn_a = logw;  // rows pass
     p->logn_b = logh;  // columns pass
+    int c = env_int("B300FFT_COLS_C", cols_width_for(logh, int64_t(1) << logw));
+    if (!cols_width_valid(logh, c) || ((int64_t(1) << logw) % c) != 0) c = cols_width_for(logh, int64_t(1) << logw);
+    if (c == 0) return FFT_ERR_UNSUPPORTED;
+    p->cols_c = c;
     const size_t ea = (size_t)pow2_table_entries(logw), eb = (size_t)pow2_table_entries(logh);
     p->off_a = 0;
     p->off_b = ea;
@@ -143,10 +239,10 @@ fft_status build_pow2_2d(fft_plan_s* p, int logh, int logw) {
     if (s != FFT_OK) return s;
     if (gen_pow2_table(p->d_tables + p->off_a, logw, 0) != cudaSuccess) return FFT_ERR_CUDA;
     if (gen_pow2_table(p->d_tables + p->off_b, logh, 0) != cudaSuccess) return FFT_ERR_CUDA;
-    if (rows_prepare(logw, false) != cudaSuccess || cols_prepare(logh, p->cols_c) != cudaSuccess) return FFT_ERR_CUDA;
+    if (rows_prepare(logw) != cudaSuccess || cols_prepare(logh, c) != cudaSuccess) return FFT_ERR_CUDA;
     p->kernels = 2;
-    std::snprintf(p->desc, sizeof p->desc, "2d H=2^%d W=2^%d: rows(tpc=%d) then cols(C=%d threads=%d)", logh,
-                  logw, rows_tpc(logw, false), p->cols_c, cols_threads(logh, p->cols_c));
+    std::snprintf(p->desc, sizeof p->desc, "2d H=2^%d W=2^%d: rows(tpc=%d) then cols(C=%d threads=%d)", logh, logw,
+                  rows_tpc(logw), c, cols_threads(logh, c));
     return FFT_OK;
 }
 

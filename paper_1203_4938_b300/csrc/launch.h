@@ -20,33 +20,50 @@ cudaError_t gen_pow2_table(float2* tw, int logn, cudaStream_t st);
 cudaError_t gen_root_table(float2* out, int64_t count, int64_t mult, int64_t n, cudaStream_t st);
 
 // --- rows kernel (k_rows.cu) ----------------------------------------------
-// Transforms-per-CTA the rows kernel uses for 2^logn (plain and transposed).
-int rows_tpc(int logn, bool transposed);
-// Dynamic shared memory bytes of that configuration.
-int rows_smem(int logn, bool transposed);
-int rows_threads(int logn, bool transposed);
-// Raise the dynamic shared-memory limit of the kernels a plan will use.
-cudaError_t rows_prepare(int logn, bool transposed);
-// nrows transforms of length 2^logn, [nrows][2^logn] -> same layout, or with
-// transposed=true the four-step output layout (see stockham_pow2.cuh).
-cudaError_t launch_rows(int logn, bool inv, bool transposed, const float2* in, float2* out, int64_t nrows,
-                        const float2* tw, int64_t n1, cudaStream_t st);
+// nrows contiguous transforms of length 2^logn, [nrows][2^logn] -> same layout.
+int rows_tpc(int logn);
+int rows_threads(int logn);
+cudaError_t rows_prepare(int logn);  // raise the dynamic shared-memory limit
+cudaError_t launch_rows(int logn, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                        cudaStream_t st);
+
+// --- transposed rows (k_rowsT.cu) -------------------------------------------
+// Four-step second pass: nrows = items * n1 rows of length 2^logn, `tpc` rows
+// per CTA (2..64, n1 % tpc == 0); row k1 of item j, bin k2 goes to
+// out[j*n1*2^logn + k1 + n1*k2].
+int rowsT_threads(int logn, int tpc);
+cudaError_t rowsT_prepare(int logn, int tpc);
+cudaError_t launch_rowsT(int logn, int tpc, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                         int64_t n1, cudaStream_t st);
 
 // --- columns kernel (k_cols.cu) -------------------------------------------
-// C = adjacent columns per CTA.  cols_width is the default for a length (the
-// only width with the four-step twiddle); cols_width_for picks the widest
-// instantiated width (default, 4 or 1) that divides ncols.
+// C = adjacent columns per CTA, a power of two in [1, 64] with
+// C * 2^logn / 16 <= 1024 threads.  cols_width is the default for a length;
+// cols_width_for the widest valid width that divides ncols (0 if none).
+bool cols_width_valid(int logn, int c);
 int cols_width(int logn);
 int cols_width_for(int logn, int64_t ncols);
-int cols_smem(int logn, int c);
 int cols_threads(int logn, int c);
 cudaError_t cols_prepare(int logn, int c);
 // Column transforms of length 2^logn over `ncols` adjacent columns of each of
 // `nitems` row-major [2^logn][S] arrays (item_stride elements apart).  With
-// twiddle_out (default width only), element (k1, n2) is multiplied by
-// W_{2^logn * S}^{n2*k1} from the two-level table (lo, hi, sh).
+// twiddle_out, element (k1, n2) is multiplied by W_{2^logn * S}^{n2*k1} from
+// the two-level table (lo, hi, sh).
 cudaError_t launch_cols(int logn, int c, bool inv, bool twiddle_out, const float2* in, float2* out, int64_t S,
                         int64_t ncols, int64_t item_stride, int64_t nitems, const float2* tw, const float2* lo,
                         const float2* hi, int sh, cudaStream_t st);
+
+// --- persistent four-step (k_persist.cu) -----------------------------------
+struct PersistArgs;  // persist.cuh
+struct PersistConfig {
+    int l1, c, l2, tpc;  // N = 2^l1 * 2^l2; column width c, transposed rows per CTA tpc
+};
+struct PersistInfo {
+    int threads = 0, smem = 0, blocks_per_sm = 0;
+};
+bool persist_config_available(const PersistConfig& c);
+cudaError_t persist_prepare(const PersistConfig& c, PersistInfo* info);
+cudaError_t launch_fourstep_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid,
+                                    cudaStream_t st);
 
 }  // namespace b300fft

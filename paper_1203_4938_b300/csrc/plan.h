@@ -13,6 +13,7 @@ enum class PlanKind : int {
     None = 0,
     Rows,      // single-pass power-of-two rows kernel
     FourStep,  // columns + transposed rows, through the workspace
+    FourStepPersist,  // both four-step passes in one persistent launch, L2-resident chunks
     TwoD,      // rows pass then in-place columns pass
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
@@ -34,11 +35,19 @@ struct fft_plan_s {
     int64_t elements = 0;  // complex elements per exec (in and out)
     int precision = 0;
     b300fft::PlanKind kind = b300fft::PlanKind::None;
-    int single_max_log = 12;  // largest power-of-two length done in one pass
+    int single_max_log = 14;  // largest power-of-two length done in one pass
 
     // power-of-two kernels
     int logn_a = 0, logn_b = 0, sh = 0;
-    int cols_c = 0;  // columns kernel width
+    int cols_c = 0;     // columns kernel width
+    int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA
+
+    // persistent four-step
+    int pl1 = 0, pc = 0, pl2 = 0, ptpc = 0;
+    int pgrid = 0, pnch = 0, pna = 0, pnb = 0;
+    int64_t pcb = 0;
+    int64_t spin_limit = int64_t(1) << 23;
+    int withhold_chunk = -1;
     size_t off_a = 0, off_b = 0, off_lo = 0, off_hi = 0;  // into d_tables (float2 units)
 
     float2* d_tables = nullptr;

@@ -59,6 +59,38 @@ __host__ __device__ __forceinline__ constexpr int padi(int a) { return a + (a >>
 __device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
 __device__ __forceinline__ void st_stream(float2* p, float2 v) { __stcs(p, v); }
 
+// Data-access flavours of the tile functions.
+//   Ld::Stream  evict-first load (input read once)
+//   Ld::Cg      L2-only load (workspace written earlier in the same launch)
+//   St::Stream  evict-first store (final output)
+//   St::Keep    store with an L2 evict-last policy (workspace read back soon)
+enum class Ld { Stream, Cg };
+enum class St { Stream, Keep };
+
+template <Ld K>
+__device__ __forceinline__ float2 ldx(const float2* p) {
+    if constexpr (K == Ld::Stream) return __ldcs(p);
+    else return __ldcg(p);
+}
+template <St K>
+__device__ __forceinline__ void stx(float2* p, float2 v, uint64_t pol) {
+    if constexpr (K == St::Stream) {
+        __stcs(p, v);
+    } else {
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// Drop a 128-byte L2 line without writing it back (scratch data only).
+__device__ __forceinline__ void l2_discard_line(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 template <int R, int S, bool INV>
 __device__ __forceinline__ void dft_at(float2* v) {
     dft<R, 0, S, INV>(v);
@@ -133,119 +165,192 @@ __device__ __forceinline__ void run_passes(float2 (&v)[PL::R], int t, float2* s,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Rows kernel: TPC contiguous transforms of length N per CTA ([batch][N]).
-// TRANSPOSE_OUT (four-step second pass): the CTA's TPC rows are consecutive
-// k1 of one item of N1*N elements and the result of row k1, bin k2 goes to
-// out[item*N1*N + k1 + N1*k2]; it is staged in shared memory so that the
-// global stores run TPC consecutive k1 at a time.
-// ---------------------------------------------------------------------------
-template <int LOGN, int TPC>
-struct RowsCfg {
-    using PL = P2Plan<LOGN>;
-    static constexpr int THREADS = PL::T * TPC;
-    static constexpr bool WARP_ONLY = (PL::T <= 32) && (32 % PL::T == 0) && false;
-    // transposed staging: row pitch chosen so that TPC rows read at the same
-    // column index fall in distinct banks (pitch = 16/TPC mod 16, in float2).
-    static constexpr int PITCH_T = ((PL::PADDED + 15) / 16) * 16 + (TPC >= 16 ? 1 : 16 / TPC);
-    static constexpr int SMEM_PLAIN = (PL::NPASS > 1 ? PL::PADDED * TPC : 0) * 8;
-    static constexpr int SMEM_T = PITCH_T * TPC * 8;
-};
-
-template <int LOGN, int TPC, bool INV, bool TRANSPOSE_OUT>
-__global__ void __launch_bounds__(RowsCfg<LOGN, TPC>::THREADS)
-k_rows_pow2(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows,
-            const float2* __restrict__ tw, int64_t n1) {
-    using CF = RowsCfg<LOGN, TPC>;
-    using PL = typename CF::PL;
-    extern __shared__ float2 smem[];
-    const int t = threadIdx.x & (PL::T - 1);
-    const int sub = threadIdx.x / PL::T;
-    const int64_t row0 = (int64_t)blockIdx.x * TPC;
-    const int64_t row = row0 + sub;
-    const bool ok = row < nrows;
-    const float2* src = in + row * PL::N;
-    float2 v[PL::R];
-#pragma unroll
-    for (int i = 0; i < PL::R; ++i) v[i] = ok ? ld_stream(src + t + i * PL::T) : make_float2(0.f, 0.f);
-
-    constexpr int pitch = TRANSPOSE_OUT ? CF::PITCH_T : PL::PADDED;
-    float2* s = smem + sub * pitch;
-    run_passes<PL, 0, INV, CF::WARP_ONLY>(v, t, s, 1, 0, tw);
-
-    if constexpr (!TRANSPOSE_OUT) {
-        float2* dst = out + row * PL::N;
-        if (ok) {
-#pragma unroll
-            for (int i = 0; i < PL::R; ++i) st_stream(dst + t + i * PL::T, v[i]);
-        }
-    } else {
-        // last pass output is x[t + i*T] in natural order: stage it, then
-        // store TPC consecutive k1 for each k2.
-#pragma unroll
-        for (int i = 0; i < PL::R; ++i) s[padi(t + i * PL::T)] = v[i];
+// Passes P .. NPASS-2, ending with the scatter of the inputs of the last pass
+// into the exchange buffer and a barrier (the caller gathers them with its own
+// thread mapping).  Requires NPASS >= 2.
+template <class PL, int P, bool INV>
+__device__ __forceinline__ void run_passes_to_last(float2 (&v)[PL::R], int t, float2* s,
+                                                   const float2* __restrict__ tw) {
+    pass_compute<PL, P, INV>(v, t, tw);
+    pass_scatter<PL, P>(v, t, s, 1, 0);
+    __syncthreads();
+    if constexpr (P + 2 < PL::NPASS) {
+        pass_gather<PL>(v, t, s, 1, 0);
         __syncthreads();
-        const int64_t item = row0 / n1;
-        const int64_t k10 = row0 - item * n1;
-        float2* dst = out + item * n1 * PL::N + k10;
-        constexpr int TOT = TPC * PL::N;
-#pragma unroll 4
-        for (int e = threadIdx.x; e < TOT; e += CF::THREADS) {
-            const int c = e % TPC, k2 = e / TPC;
-            if (row0 + c < nrows) st_stream(dst + c + n1 * (int64_t)k2, smem[c * pitch + padi(k2)]);
-        }
+        run_passes_to_last<PL, P + 1, INV>(v, t, s, tw);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Columns kernel: C adjacent columns of a row-major [len][S] array per CTA,
-// each column a transform of length N = 2^LOGN with element stride S.
-// Used for the 2-D column pass (S = W) and the four-step first pass (S = N2),
-// where TWIDDLE_OUT multiplies element (k1, n2) by W_{N*S}^{n2*k1} from the
-// two-level table W(m) = hi[m >> sh] * lo[m & (2^sh - 1)].
+// Tile functions.  Each processes one tile with all threads of the CTA (the
+// thread count must equal the tile's THREADS) and may be called repeatedly by
+// a persistent CTA; the caller separates consecutive tiles with a barrier.
+// ---------------------------------------------------------------------------
+
+// Rows tile: TPC contiguous transforms of length N ([TPC][N] at src/dst);
+// rows >= nrows are skipped (their threads still take part in the barriers).
+template <int LOGN, int TPC>
+struct RowsCfg {
+    using PL = P2Plan<LOGN>;
+    static constexpr int THREADS = PL::T * TPC;
+    static constexpr int SMEM = (PL::NPASS > 1 ? PL::PADDED * TPC : 0) * 8;
+};
+
+template <int LOGN, int TPC, bool INV, Ld LK, St SK>
+__device__ __forceinline__ void rows_tile(const float2* __restrict__ src, float2* __restrict__ dst, int nrows,
+                                          const float2* __restrict__ tw, float2* smem, uint64_t pol) {
+    using PL = typename RowsCfg<LOGN, TPC>::PL;
+    const int t = threadIdx.x & (PL::T - 1);
+    const int sub = threadIdx.x / PL::T;
+    const bool ok = sub < nrows;
+    src += (int64_t)sub * PL::N;
+    dst += (int64_t)sub * PL::N;
+    float2 v[PL::R];
+#pragma unroll
+    for (int i = 0; i < PL::R; ++i) v[i] = ok ? ldx<LK>(src + t + i * PL::T) : make_float2(0.f, 0.f);
+    run_passes<PL, 0, INV, false>(v, t, smem + sub * PL::PADDED, 1, 0, tw);
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < PL::R; ++i) stx<SK>(dst + t + i * PL::T, v[i], pol);
+    }
+}
+
+// Transposed rows tile (four-step second pass).  src = TPC consecutive rows
+// k1_0 .. k1_0+TPC-1 of one item ([TPC][N] contiguous); bin k2 of row
+// k1_0 + c goes to dst[c + n1*k2] (dst = item base + k1_0).  All passes but
+// the last run with thread (row, t); the last pass is re-mapped to thread
+// (t', row) with the row index fastest, so the global stores write TPC
+// consecutive k1 (TPC*8 bytes) for each k2 straight from registers.  Row
+// pitch in shared memory is congruent to 16/TPC (mod 16) float2, so the
+// re-mapped gather is bank-conflict free.
+template <int LOGN, int TPC>
+struct RowsTCfg {
+    using PL = P2Plan<LOGN>;
+    static constexpr int THREADS = PL::T * TPC;
+    static constexpr int PITCH = ((PL::PADDED + 15) / 16) * 16 + (TPC >= 16 ? 1 : 16 / TPC);
+    static constexpr int SMEM = PITCH * TPC * 8;
+};
+
+template <int LOGN, int TPC, bool INV, Ld LK, St SK>
+__device__ __forceinline__ void rowsT_tile(const float2* __restrict__ src, float2* __restrict__ dst, int64_t n1,
+                                           const float2* __restrict__ tw, float2* smem, uint64_t pol) {
+    using CF = RowsTCfg<LOGN, TPC>;
+    using PL = typename CF::PL;
+    static_assert(PL::NPASS >= 2, "transposed rows need at least two passes");
+    const int t = threadIdx.x & (PL::T - 1);
+    const int sub = threadIdx.x / PL::T;
+    const float2* s0 = src + (int64_t)sub * PL::N;
+    float2 v[PL::R];
+#pragma unroll
+    for (int i = 0; i < PL::R; ++i) v[i] = ldx<LK>(s0 + t + i * PL::T);
+    run_passes_to_last<PL, 0, INV>(v, t, smem + sub * CF::PITCH, tw);
+    const int c = threadIdx.x % TPC;
+    const int t2 = threadIdx.x / TPC;
+    const float2* sc = smem + c * CF::PITCH;
+#pragma unroll
+    for (int i = 0; i < PL::R; ++i) v[i] = sc[padi(t2 + i * PL::T)];
+    pass_compute<PL, PL::NPASS - 1, INV>(v, t2, tw);
+    float2* d0 = dst + c;
+#pragma unroll
+    for (int i = 0; i < PL::R; ++i) stx<SK>(d0 + n1 * (int64_t)(t2 + i * PL::T), v[i], pol);
+}
+
+// Columns tile: C adjacent columns of a row-major [N][S] array (src/dst point
+// at the tile's first column), each column a transform of length N with
+// element stride S.  Used for the 2-D column pass (S = W) and the four-step
+// first pass (S = N2), where TW multiplies element (k1, n2) by
+// W_{N*S}^{n2*k1}, n2 = col0 + c.  With k1 = t + i*T that factor is
+// W^{n2*t} * W^{n2*T*i}: the first is read once per thread and the second
+// once per (column, i) into shared memory, each from the two-level table
+// W(m) = hi[m >> sh] * lo[m & (2^sh - 1)] (m < N*S, no reduction needed).
 // Thread (c, t): c = threadIdx.x % C is the column (fastest, so each warp
 // touches C*8 contiguous bytes per row), t the Stockham thread index.
-// ---------------------------------------------------------------------------
 template <int LOGN, int C>
 struct ColsCfg {
     using PL = P2Plan<LOGN>;
     static constexpr int THREADS = PL::T * C;
-    static constexpr int SMEM = (PL::NPASS > 1 ? padi(PL::N * C) : 0) * 8;
+    static constexpr int XBUF = PL::NPASS > 1 ? padi(PL::N * C) : 0;  // float2
+    static constexpr int SMEM = (XBUF + C * PL::R) * 8;
 };
 
-template <int LOGN, int C, bool INV, bool TWIDDLE_OUT>
-__global__ void __launch_bounds__(ColsCfg<LOGN, C>::THREADS)
-k_cols_pow2(const float2* __restrict__ in, float2* __restrict__ out, int64_t S, int64_t ngroups_per_item,
-            int64_t item_stride, int64_t nitems, const float2* __restrict__ tw,
-            const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi, int sh) {
+__device__ __forceinline__ float2 root2(const float2* __restrict__ lo, const float2* __restrict__ hi, uint32_t m,
+                                        int sh) {
+    return cmul(__ldg(hi + (m >> sh)), __ldg(lo + (m & ((1u << sh) - 1u))));
+}
+
+template <int LOGN, int C, bool INV, bool TW, Ld LK, St SK>
+__device__ __forceinline__ void cols_tile(const float2* __restrict__ src, float2* __restrict__ dst, int64_t S,
+                                          uint32_t col0, const float2* __restrict__ tw,
+                                          const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi, int sh,
+                                          float2* smem, uint64_t pol) {
     using CF = ColsCfg<LOGN, C>;
     using PL = typename CF::PL;
-    extern __shared__ float2 smem[];
     const int c = threadIdx.x % C;
     const int t = threadIdx.x / C;
-    const int64_t item = blockIdx.x / ngroups_per_item;
-    const int64_t g = blockIdx.x - item * ngroups_per_item;
-    if (item >= nitems) return;  // uniform per CTA
-    const int64_t col = g * C + c;
-    const float2* src = in + item * item_stride + col;
+    src += c;
     float2 v[PL::R];
 #pragma unroll
-    for (int i = 0; i < PL::R; ++i) v[i] = ld_stream(src + (int64_t)(t + i * PL::T) * S);
+    for (int i = 0; i < PL::R; ++i) v[i] = ldx<LK>(src + (int64_t)(t + i * PL::T) * S);
+
+    float2* steps = smem + CF::XBUF;  // [R][C]: W^{n2*T*i} (column fastest: conflict-free reads)
+    if constexpr (TW) {
+        for (int j = threadIdx.x; j < C * PL::R; j += CF::THREADS) {
+            const int cc = j % C, ii = j / C;
+            steps[ii * C + cc] = root2(tw_lo, tw_hi, (col0 + (uint32_t)cc) * (uint32_t)(ii * PL::T), sh);
+        }
+        if constexpr (PL::NPASS == 1) __syncthreads();
+    }
 
     run_passes<PL, 0, INV, false>(v, t, smem, C, c, tw);
 
-    if constexpr (TWIDDLE_OUT) {
-        const uint32_t mask = (1u << sh) - 1u;
+    if constexpr (TW) {
+        const float2 w0 = root2(tw_lo, tw_hi, (col0 + (uint32_t)c) * (uint32_t)t, sh);
 #pragma unroll
-        for (int i = 0; i < PL::R; ++i) {
-            const uint32_t m = (uint32_t)col * (uint32_t)(t + i * PL::T);
-            const float2 w = cmul(__ldg(tw_hi + (m >> sh)), __ldg(tw_lo + (m & mask)));
-            v[i] = twmul<INV>(v[i], w);
-        }
+        for (int i = 0; i < PL::R; ++i) v[i] = twmul<INV>(v[i], cmul(w0, steps[i * C + c]));
     }
-    float2* dst = out + item * item_stride + col;
+    dst += c;
 #pragma unroll
-    for (int i = 0; i < PL::R; ++i) st_stream(dst + (int64_t)(t + i * PL::T) * S, v[i]);
+    for (int i = 0; i < PL::R; ++i) stx<SK>(dst + (int64_t)(t + i * PL::T) * S, v[i], pol);
+}
+
+// ---------------------------------------------------------------------------
+// One-tile-per-CTA kernels.
+// ---------------------------------------------------------------------------
+template <int LOGN, int TPC, bool INV>
+__global__ void __launch_bounds__(RowsCfg<LOGN, TPC>::THREADS, 1024 / RowsCfg<LOGN, TPC>::THREADS)
+k_rows_pow2(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows, const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int64_t row0 = (int64_t)blockIdx.x * TPC;
+    const int64_t left = nrows - row0;
+    rows_tile<LOGN, TPC, INV, Ld::Stream, St::Stream>(in + row0 * (1 << LOGN), out + row0 * (1 << LOGN),
+                                                      left < TPC ? (int)left : TPC, tw, smem, 0);
+}
+
+// nrows = items * n1 rows; the CTA's TPC rows are consecutive k1 of one item.
+template <int LOGN, int TPC, bool INV>
+__global__ void __launch_bounds__(RowsTCfg<LOGN, TPC>::THREADS, 1024 / RowsTCfg<LOGN, TPC>::THREADS)
+k_rowsT_pow2(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows, const float2* __restrict__ tw,
+             int64_t n1) {
+    extern __shared__ float2 smem[];
+    const int64_t row0 = (int64_t)blockIdx.x * TPC;
+    const int64_t item = row0 / n1;
+    const int64_t k10 = row0 - item * n1;
+    rowsT_tile<LOGN, TPC, INV, Ld::Stream, St::Stream>(in + row0 * (1 << LOGN),
+                                                       out + item * n1 * (1 << LOGN) + k10, n1, tw, smem, 0);
+}
+
+template <int LOGN, int C, bool INV, bool TWIDDLE_OUT>
+__global__ void __launch_bounds__(ColsCfg<LOGN, C>::THREADS, 1024 / ColsCfg<LOGN, C>::THREADS)
+k_cols_pow2(const float2* __restrict__ in, float2* __restrict__ out, int64_t S, int64_t ngroups_per_item,
+            int64_t item_stride, int64_t nitems, const float2* __restrict__ tw,
+            const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi, int sh) {
+    extern __shared__ float2 smem[];
+    const int64_t item = blockIdx.x / ngroups_per_item;
+    const int64_t g = blockIdx.x - item * ngroups_per_item;
+    if (item >= nitems) return;  // uniform per CTA
+    const int64_t off = item * item_stride + g * C;
+    cols_tile<LOGN, C, INV, TWIDDLE_OUT, Ld::Stream, St::Stream>(in + off, out + off, S, (uint32_t)(g * C), tw,
+                                                                 tw_lo, tw_hi, sh, smem, 0);
 }
 
 }  // namespace b300fft
