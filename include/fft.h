@@ -104,6 +104,13 @@ FFT_API fft_status fft_last_error(void);
  * direction: FFT_FORWARD or FFT_INVERSE.  Asynchronous; allocates nothing. */
 FFT_API fft_status fft_exec(fft_plan plan, const void *in, void *out, int direction, void *stream);
 
+/* Same result and arguments as fft_exec, but for plans built by the
+ * stage-graph executor (ragged plans and non-power-of-two lengths) it enqueues
+ * one kernel launch per (stage, length) group, in dependency order, instead of
+ * the single persistent launch: the per-size-launch baseline the persistent
+ * form is compared against.  For other plans it is fft_exec. */
+FFT_API fft_status fft_exec_per_size(fft_plan plan, const void *in, void *out, int direction, void *stream);
+
 /* Read and clear the plan's device status word (synchronous; call it after
  * the stream that ran fft_exec has been synchronised). */
 FFT_API fft_status fft_plan_check(fft_plan plan);

@@ -1,11 +1,13 @@
 // exec.cu -- fft_exec dispatch: enqueue the kernels of a plan on a stream.
+#include "gplan.h"
 #include "launch.h"
 #include "persist.cuh"
 #include "plan.h"
 
 namespace b300fft {
 
-fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only) {
+fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only,
+                     bool per_size) {
     cudaError_t e = cudaSuccess;
     auto want = [only](int k) { return only < 0 || only == k; };
     switch (p->kind) {
@@ -55,13 +57,16 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                                 nullptr, nullptr, 0, st);
             break;
         }
+        case PlanKind::Generic:
+        case PlanKind::Ragged:
+            if (!want(0)) return FFT_OK;
+            return graph_plan_exec(p->gplan, in, out, inv, st, p->d_status, per_size);
         default:
             return FFT_ERR_UNSUPPORTED;
     }
     return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
 }
 
-fft_status build_generic_1d(fft_plan_s*) { return FFT_ERR_UNSUPPORTED; }
 fft_status build_tc_plan(fft_plan_s*) { return FFT_ERR_UNSUPPORTED; }
 
 }  // namespace b300fft

@@ -16,6 +16,7 @@
 #include <string>
 
 #include "../../include/fft.h"
+#include "gplan.h"
 #include "launch.h"
 #include "persist.cuh"
 #include "plan.h"
@@ -66,6 +67,11 @@ void destroy_plan_resources(fft_plan_s* p) {
     p->d_work = nullptr;
     p->d_status = nullptr;
     p->d_aux = nullptr;
+    if (p->gplan) {
+        graph_plan_free(p->gplan);
+        delete p->gplan;
+        p->gplan = nullptr;
+    }
 }
 
 }  // namespace b300fft
@@ -246,7 +252,47 @@ fft_status build_pow2_2d(fft_plan_s* p, int logh, int logw) {
     return FFT_OK;
 }
 
+fft_plan finish(fft_plan_s* p) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(FFT_ERR_CUDA, p);
+    p->magic = kPlanMagic;
+    {
+        std::lock_guard<std::mutex> lk(g_registry_mu);
+        g_registry.insert(p);
+    }
+    return p;
+}
+
 }  // namespace
+
+namespace b300fft {
+
+// Non-power-of-two 1-D lengths: mixed radix 2/3/4/5/7/8/16 (single tile or
+// four-step) or Bluestein, through the stage-graph executor.
+fft_status build_generic_1d(fft_plan_s* p) {
+    p->gplan = new (std::nothrow) GraphPlan();
+    if (!p->gplan) return FFT_ERR_ALLOC;
+    fft_status s = graph_plan_build(p->gplan, std::vector<int64_t>{p->len[0]}, p->batch, false);
+    if (s != FFT_OK) return s;
+    p->kind = PlanKind::Generic;
+    p->kernels = 1;
+    p->work_bytes = p->gplan->work_bytes;
+    std::snprintf(p->desc, sizeof p->desc, "generic N=%lld: %s", (long long)p->len[0], p->gplan->desc.c_str());
+    return FFT_OK;
+}
+
+fft_status build_ragged(fft_plan_s* p, const int64_t* lengths, int64_t count) {
+    p->gplan = new (std::nothrow) GraphPlan();
+    if (!p->gplan) return FFT_ERR_ALLOC;
+    fft_status s = graph_plan_build(p->gplan, std::vector<int64_t>(lengths, lengths + count), count, true);
+    if (s != FFT_OK) return s;
+    p->kind = PlanKind::Ragged;
+    p->kernels = 1;
+    p->work_bytes = p->gplan->work_bytes;
+    std::snprintf(p->desc, sizeof p->desc, "ragged count=%lld: %s", (long long)count, p->gplan->desc.c_str());
+    return FFT_OK;
+}
+
+}  // namespace b300fft
 
 extern "C" {
 
@@ -285,16 +331,43 @@ fft_plan fft_plan_create(int dims, const int64_t* lengths, int64_t batch, int pr
         else s = FFT_ERR_UNSUPPORTED;
     }
     if (s != FFT_OK) return fail(s, p);
-    if (cudaDeviceSynchronize() != cudaSuccess) return fail(FFT_ERR_CUDA, p);
-    p->magic = kPlanMagic;
-    {
-        std::lock_guard<std::mutex> lk(g_registry_mu);
-        g_registry.insert(p);
+    return finish(p);
+}
+
+fft_plan fft_plan_create_ragged(const int64_t* lengths, int64_t count, int precision) {
+    g_last_error = FFT_OK;
+    if (!lengths || count < 1 || count > (int64_t(1) << 24)) return fail(FFT_ERR_INVALID_ARG, nullptr);
+    if (precision < FFT_FP32 || precision > FFT_TC_BF16_PLAIN) return fail(FFT_ERR_INVALID_ARG, nullptr);
+    int64_t total = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (lengths[i] < 1 || lengths[i] > (int64_t(1) << 20)) return fail(FFT_ERR_INVALID_ARG, nullptr);
+        total += lengths[i];
     }
-    return p;
+    if (precision != FFT_FP32) return fail(FFT_ERR_UNSUPPORTED, nullptr);
+    fft_plan_s* p = new (std::nothrow) fft_plan_s();
+    if (!p) return fail(FFT_ERR_ALLOC, nullptr);
+    p->dims = 1;
+    p->batch = count;
+    p->precision = precision;
+    p->elements = total;
+    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_ALLOC, p);
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_CUDA, p);
+    fft_status s = build_ragged(p, lengths, count);
+    if (s != FFT_OK) return fail(s, p);
+    return finish(p);
 }
 
 fft_status fft_last_error(void) { return g_last_error; }
+
+fft_status fft_exec_per_size(fft_plan plan, const void* in, void* out, int direction, void* stream) {
+    if (!is_registered(plan)) return FFT_ERR_BAD_HANDLE;
+    if (!in || !out) return FFT_ERR_INVALID_ARG;
+    if (direction != FFT_FORWARD && direction != FFT_INVERSE) return FFT_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return FFT_ERR_MISALIGNED;
+    return exec_plan(plan, static_cast<const float2*>(in), static_cast<float2*>(out), direction == FFT_INVERSE,
+                     static_cast<cudaStream_t>(stream), -1, true);
+}
 
 fft_status fft_exec(fft_plan plan, const void* in, void* out, int direction, void* stream) {
     if (!is_registered(plan)) return FFT_ERR_BAD_HANDLE;

@@ -1,0 +1,282 @@
+// generic.cuh -- runtime mixed-radix Stockham tiles and the stage-graph
+// executor used for non-power-of-two lengths, Bluestein's algorithm and the
+// ragged (uneven-length) batch.
+//
+// A transform is a short chain of *stages*; a stage is a set of independent
+// *tiles*; a tile transforms `nl` lines of one length L = R_0*R_1*...
+// (radices 2,3,4,5,7,8,16) inside one CTA:
+//   1. coalesced load of the tile into shared memory (optionally multiplied
+//      by a table, zero at offsets >= in_valid),
+//   2. Stockham passes between two shared-memory buffers (the pass formula of
+//      the power-of-two kernels, with runtime radices),
+//   3. the last pass stores to global memory, optionally multiplied by the
+//      four-step twiddle W_{lines*L}^{line*k} or by a table, and only at
+//      offsets < out_valid.
+// Chains (the paper's Sec. III-A Cooley-Tukey split N = N1*N2, and the
+// chirp-z rewrite n*k = (n^2 + k^2 - (k-n)^2)/2 for awkward lengths):
+//   single      in -> out                                   (L <= tile max)
+//   four-step   A: columns (L=N1, stride N2) x W_N^{n2 k1} -> work1
+//               B: rows (L=N2) stored transposed             -> out
+//   Bluestein   FFT_M of x*w (zero padded), x filter, IFFT_M, x w,
+//               as 2 single-tile stages or 4 four-step stages.
+// Every tile of stage s of a transform waits (bounded) for all tiles of
+// stage s-1 of the same transform; the executor dequeues tiles from one
+// atomic counter in an order where dependencies always come first.
+#pragma once
+#include "butterfly.cuh"
+#include "persist.cuh"
+
+namespace b300fft {
+
+constexpr int kGMaxPass = 8;
+constexpr int kGTileMax = 4096;  // complex elements per tile (lines * L)
+constexpr int kGMaxLines = 128;
+constexpr int kGThreads = 256;
+constexpr int kGBuf = kGTileMax + kGTileMax / 16 + kGMaxLines;  // float2 per smem buffer
+constexpr int kGSmem = 2 * kGBuf * 8;
+
+struct GShape {
+    int L, npass;
+    int radix[kGMaxPass];
+    int ns[kGMaxPass];
+    int64_t tw[kGMaxPass];  // offset of pass p's table in the pool (p >= 1)
+};
+
+enum : int { G_PRE_NONE = 0, G_PRE_TABLE = 1, G_PRE_TABLE_CONJ = 2 };
+enum : int { G_POST_NONE = 0, G_POST_TW4 = 1, G_POST_TABLE = 2, G_POST_TABLE_CONJ = 3 };
+enum : int { G_BUF_IN = 0, G_BUF_OUT = 1, G_BUF_W1 = 2, G_BUF_W2 = 3 };
+
+struct GStage {
+    int shape;  // GShape index
+    int nlines, lpt, ntiles;
+    int in_buf, out_buf;
+    int in_line_fast;   // 1: load with the line index fastest (column tiles)
+    int out_line_fast;  // 1: last pass with the line index fastest (transposed stores)
+    int inv;            // direction of this stage's transform
+    int pre, post;
+    int sh;
+    int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
+    int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
+    int64_t pre_tab, post_tab;             // table offsets in the pool
+    int64_t lo, hi;                        // four-step two-level table in the pool
+};
+
+struct GTransform {
+    int kind;  // index of its first stage in the stage array
+    int nstages;
+    int ctr;  // first of its nstages-1 dependency counters
+    int pad_;
+    int64_t in_off, out_off, w1_off, w2_off;
+};
+
+struct GExecArgs {
+    const float2* in;
+    float2* out;
+    float2* work;
+    const float2* pool;  // twiddle / chirp / filter tables
+    const GShape* shapes;
+    const GStage* stages;  // for this direction
+    const GTransform* xf;
+    const uint64_t* items;  // (transform << 32) | (stage << 24) | tile
+    int nitems;
+    int* ctl;  // [0] queue head, [1 + c] dependency counters
+    int* status;
+    int64_t spin_limit;
+    int single;  // per-stage launch: item = item0 + blockIdx.x, no waits
+    int item0;
+};
+
+__device__ __forceinline__ int gpad(int a) { return a + (a >> 4); }
+
+// Pass p of a tile: every radix-R butterfly of nl lines.  Intermediate passes
+// go src -> dst in shared memory; the last pass stores to global memory.
+template <int R, bool INV>
+__device__ __forceinline__ void g_pass(const GStage& st, const GShape& sh, int p, const float2* __restrict__ pool,
+                                       const float2* src, float2* dst, int Lp, int line0, int nl, bool last,
+                                       float2* __restrict__ gout) {
+    const int L = sh.L;
+    const int Ns = sh.ns[p];
+    const int stride = L / R;  // butterflies per line
+    const int nbf = nl * stride;
+    const float2* tw = pool + sh.tw[p];
+    const bool lf = last && st.out_line_fast;
+    for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
+        int line, b;
+        if (lf) {
+            line = bf % nl;
+            b = bf / nl;
+        } else {
+            line = bf / stride;
+            b = bf - line * stride;
+        }
+        const float2* s = src + line * Lp;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = s[gpad(b + r * stride)];
+        const int k = b % Ns;
+        if (p > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = twmul<INV>(v[r], __ldg(tw + (r - 1) * Ns + k));
+        }
+        dft<R, 0, 1, INV>(v);
+        if (!last) {
+            float2* d = dst + line * Lp;
+            const int base = (b - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[gpad(base + r * Ns)] = v[r];
+        } else {
+            // natural order: output element k = b + r*stride of line line0+line
+            const int aline = line0 + line;
+            const int64_t lo_line = (int64_t)aline * st.out_ls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int kk = b + r * stride;
+                const int64_t off = lo_line + (int64_t)kk * st.out_es;
+                if (off >= st.out_valid) continue;
+                float2 val = v[r];
+                if (st.post == G_POST_TW4) {
+                    const uint32_t m = (uint32_t)aline * (uint32_t)kk;
+                    val = twmul<INV>(val, root2(pool + st.lo, pool + st.hi, m, st.sh));
+                } else if (st.post == G_POST_TABLE) {
+                    val = cmul(val, __ldg(pool + st.post_tab + off));
+                } else if (st.post == G_POST_TABLE_CONJ) {
+                    val = cmulc(val, __ldg(pool + st.post_tab + off));
+                }
+                __stcg(gout + off, val);
+            }
+        }
+    }
+}
+
+// One tile: lines [line0, line0 + nl) of a stage.
+template <bool INV>
+__device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __restrict__ pool,
+                           const float2* __restrict__ gin, float2* __restrict__ gout, int line0, int nl,
+                           float2* smem) {
+    const int L = sh.L;
+    const int Lp = gpad(L) + 1;
+    float2* bufA = smem;
+    float2* bufB = smem + kGBuf;
+    // 1. load (coalesced), pre-multiply, zero beyond in_valid
+    const int tot = nl * L;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int line, i;
+        if (st.in_line_fast) {
+            line = e % nl;
+            i = e / nl;
+        } else {
+            line = e / L;
+            i = e - line * L;
+        }
+        const int64_t off = (int64_t)(line0 + line) * st.in_ls + (int64_t)i * st.in_es;
+        float2 v = make_float2(0.f, 0.f);
+        if (off < st.in_valid) {
+            v = __ldcg(gin + off);
+            if (st.pre == G_PRE_TABLE) v = cmul(v, __ldg(pool + st.pre_tab + off));
+            else if (st.pre == G_PRE_TABLE_CONJ) v = cmulc(v, __ldg(pool + st.pre_tab + off));
+        }
+        bufA[line * Lp + gpad(i)] = v;
+    }
+    __syncthreads();
+    // 2./3. Stockham passes; the last one stores to global memory
+    const float2* src = bufA;
+    float2* dst = bufB;
+    for (int p = 0; p < sh.npass; ++p) {
+        const bool last = p + 1 == sh.npass;
+        switch (sh.radix[p]) {
+#define B300_G(RR)                                                                    \
+    case RR:                                                                          \
+        g_pass<RR, INV>(st, sh, p, pool, src, dst, Lp, line0, nl, last, gout);        \
+        break;
+            B300_G(1) B300_G(2) B300_G(3) B300_G(4) B300_G(5) B300_G(7) B300_G(8) B300_G(16)
+#undef B300_G
+            default:
+                break;
+        }
+        __syncthreads();
+        const float2* t = src;
+        src = dst;
+        dst = const_cast<float2*>(t);
+    }
+}
+
+__device__ __forceinline__ const float2* g_buf_in(const GExecArgs& a, const GTransform& x, int sel) {
+    switch (sel) {
+        case G_BUF_IN: return a.in + x.in_off;
+        case G_BUF_OUT: return a.out + x.out_off;
+        case G_BUF_W1: return a.work + x.w1_off;
+        default: return a.work + x.w2_off;
+    }
+}
+__device__ __forceinline__ float2* g_buf_out(const GExecArgs& a, const GTransform& x, int sel) {
+    switch (sel) {
+        case G_BUF_OUT: return a.out + x.out_off;
+        case G_BUF_W1: return a.work + x.w1_off;
+        case G_BUF_W2: return a.work + x.w2_off;
+        default: return a.out + x.out_off;  // never written
+    }
+}
+
+// Run queue item p (tile of one stage of one transform).
+__device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* smem, int* s_ok) {
+    const uint64_t it = a.items[p];
+    const int t = (int)(it >> 32);
+    const int s = (int)((it >> 24) & 0xff);
+    const int tile = (int)(it & 0xffffff);
+    const GTransform x = a.xf[t];
+    const GStage st = a.stages[x.kind + s];
+    const GShape sh = a.shapes[st.shape];
+    if (s > 0 && !a.single) {
+        if (threadIdx.x == 0) {
+            const int need = a.stages[x.kind + s - 1].ntiles;
+            int ok = 1;
+            int64_t spins = 0;
+            while (ld_acquire_gpu(a.ctl + 1 + x.ctr + s - 1) < need) {
+                if (++spins > a.spin_limit) {
+                    ok = 0;
+                    atomicCAS(a.status, 0, 6);
+                    break;
+                }
+                __nanosleep(128);
+            }
+            *s_ok = ok;
+        }
+        __syncthreads();
+        if (!*s_ok) return;
+    }
+    const int line0 = tile * st.lpt;
+    const int nl = min(st.lpt, st.nlines - line0);
+    const float2* gin = g_buf_in(a, x, st.in_buf);
+    float2* gout = g_buf_out(a, x, st.out_buf);
+    if (st.inv) g_tile_dir<true>(st, sh, a.pool, gin, gout, line0, nl, smem);
+    else g_tile_dir<false>(st, sh, a.pool, gin, gout, line0, nl, smem);
+    if (s + 1 < x.nstages && !a.single) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.ctl + 1 + x.ctr + s, 1);
+        }
+    }
+}
+
+// Persistent executor (single = 0) or one launch per stage group (single = 1:
+// block b runs item item0 + b; the stream orders the stages).
+__global__ void __launch_bounds__(kGThreads, 3) k_gexec(GExecArgs a) {
+    extern __shared__ float2 smem[];
+    __shared__ int s_item[2];
+    __shared__ int s_ok;
+    if (a.single) {
+        g_run_item(a, a.item0 + blockIdx.x, smem, &s_ok);
+        return;
+    }
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl, 1);
+    for (int it = 0;; it ^= 1) {
+        __syncthreads();
+        const int p = s_item[it];
+        if (p >= a.nitems) break;
+        if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.ctl, 1);
+        g_run_item(a, p, smem, &s_ok);
+    }
+}
+
+}  // namespace b300fft

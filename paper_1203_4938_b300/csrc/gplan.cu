@@ -1,0 +1,584 @@
+// gplan.cu -- host side of the stage-graph engine (generic.cuh): radix
+// plans, stage chains, the table pool, the work queue and its execution as
+// one persistent launch (captured in a CUDA graph) or as per-stage launches.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <vector>
+
+#include "generic.cuh"
+#include "gplan.h"
+#include "launch.h"
+
+namespace b300fft {
+
+namespace {
+
+int env_i(const char* name, int dflt) {
+    const char* v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+bool is_smooth(int64_t n) {
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Radix sequence of a smooth length <= kGTileMax: 16s first, then the rest
+// of the power of two, then 3, 5, 7 factors.
+bool radix_plan(int L, std::vector<int>* r) {
+    r->clear();
+    if (L == 1) {
+        r->push_back(1);
+        return true;
+    }
+    int m = L, p2 = 0;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++p2;
+    }
+    while (p2 >= 4) {
+        r->push_back(16);
+        p2 -= 4;
+    }
+    if (p2) r->push_back(1 << p2);
+    for (int p : {3, 5, 7})
+        while (m % p == 0) {
+            r->push_back(p);
+            m /= p;
+        }
+    return m == 1 && (int)r->size() <= kGMaxPass;
+}
+
+struct Builder {
+    std::vector<GShape> shapes;
+    std::map<int, int> shape_of;  // L -> index
+    std::vector<GStage> st_f, st_i;
+    std::map<int64_t, std::pair<int64_t, int64_t>> fourstep_tabs;  // N -> (lo, hi)
+    std::map<int64_t, std::array<int64_t, 3>> blue_tabs;           // N -> (chirp, Bf fwd, Bf inv)
+    int64_t pool_size = 0;
+    // deferred table generation
+    struct PassTab {
+        int64_t off;
+        int ns, r;
+    };
+    struct RootTab {
+        int64_t off, count, mult, n;
+    };
+    struct BlueTab {
+        int64_t n, M, chirp, ff, fi;
+    };
+    std::vector<PassTab> pass_tabs;
+    std::vector<RootTab> root_tabs;
+    std::vector<BlueTab> blue_list;
+
+    int64_t alloc(int64_t n) {
+        int64_t o = pool_size;
+        pool_size += (n + 1) & ~int64_t(1);  // keep 16-byte alignment
+        return o;
+    }
+    int shape(int L) {
+        auto it = shape_of.find(L);
+        if (it != shape_of.end()) return it->second;
+        std::vector<int> r;
+        if (!radix_plan(L, &r)) return -1;
+        GShape s{};
+        s.L = L;
+        s.npass = (int)r.size();
+        int ns = 1;
+        for (int p = 0; p < s.npass; ++p) {
+            s.radix[p] = r[p];
+            s.ns[p] = ns;
+            if (p > 0 && r[p] > 1) {
+                s.tw[p] = alloc((int64_t)(r[p] - 1) * ns);
+                pass_tabs.push_back({s.tw[p], ns, r[p]});
+            }
+            ns *= r[p];
+        }
+        shapes.push_back(s);
+        shape_of[L] = (int)shapes.size() - 1;
+        return (int)shapes.size() - 1;
+    }
+    std::pair<int64_t, int64_t> tw4(int64_t n, int* sh) {
+        int lg = 0;
+        while ((int64_t(1) << lg) < n) ++lg;
+        *sh = (lg + 1) / 2;
+        auto it = fourstep_tabs.find(n);
+        if (it != fourstep_tabs.end()) return it->second;
+        const int64_t nlo = int64_t(1) << *sh, nhi = (n + nlo - 1) / nlo;
+        const int64_t lo = alloc(nlo), hi = alloc(nhi);
+        root_tabs.push_back({lo, nlo, 1, n});
+        root_tabs.push_back({hi, nhi, nlo, n});
+        fourstep_tabs[n] = {lo, hi};
+        return {lo, hi};
+    }
+    std::array<int64_t, 3> blue(int64_t n, int64_t M) {
+        auto it = blue_tabs.find(n);
+        if (it != blue_tabs.end()) return it->second;
+        std::array<int64_t, 3> t{alloc(n), alloc(M), alloc(M)};
+        blue_list.push_back({n, M, t[0], t[1], t[2]});
+        blue_tabs[n] = t;
+        return t;
+    }
+};
+
+GStage base_stage(int shape, int nlines, int lpt, int inv) {
+    GStage s{};
+    s.shape = shape;
+    s.nlines = nlines;
+    s.lpt = std::max(1, std::min(lpt, nlines));
+    s.ntiles = (nlines + s.lpt - 1) / s.lpt;
+    s.inv = inv;
+    s.pre = G_PRE_NONE;
+    s.post = G_POST_NONE;
+    return s;
+}
+
+int lines_per_tile(int L, int want) {
+    int cap = std::max(1, std::min(kGMaxLines, kGTileMax / L));
+    return want > 0 ? std::min(want, cap) : cap;
+}
+
+// Choose N = N1 * N2 (both <= tile max) for a smooth N; N2 a power of two
+// when possible (radix-16 rows, long transposed-store runs).
+bool split_four(int64_t n, int tile_max, int want_n2, int64_t* n1, int64_t* n2) {
+    int64_t best = -1;
+    double bestd = 1e30;
+    auto consider = [&](int64_t b) {
+        if (b < 2 || n % b) return;
+        const int64_t a = n / b;
+        if (a > tile_max || b > tile_max || a < 2) return;
+        if (!is_smooth(a) || !is_smooth(b)) return;
+        const double d = std::fabs(std::log((double)a) - std::log((double)b)) + ((b & (b - 1)) ? 1.0 : 0.0);
+        if (d < bestd) {
+            bestd = d;
+            best = b;
+        }
+    };
+    if (want_n2 > 0) consider(want_n2);
+    if (best < 0)
+        for (int64_t b = 2; b <= tile_max; ++b) consider(b);
+    if (best < 0) return false;
+    *n2 = best;
+    *n1 = n / best;
+    return true;
+}
+
+// Stages of one transform kind (length n); `lines` > 1 only for single-tile
+// uniform batches (every batch row is a line of one stage).
+bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int* nstages, int64_t* w1,
+                int64_t* w2) {
+    *w1 = *w2 = 0;
+    std::vector<GStage> f, i;
+    if (is_smooth(n) && n <= cfg.tile_max) {
+        const int sh = B.shape((int)n);
+        if (sh < 0) return false;
+        for (int d = 0; d < 2; ++d) {
+            GStage s = base_stage(sh, (int)lines, lines_per_tile((int)n, cfg.lpt_a), d);
+            s.in_buf = G_BUF_IN;
+            s.out_buf = G_BUF_OUT;
+            s.in_ls = s.out_ls = n;
+            s.in_es = s.out_es = 1;
+            s.in_valid = s.out_valid = lines * n;
+            (d ? i : f).push_back(s);
+        }
+    } else if (is_smooth(n)) {
+        int64_t n1, n2;
+        if (!split_four(n, cfg.tile_max, cfg.split_n2, &n1, &n2)) return false;
+        const int sa = B.shape((int)n1), sb = B.shape((int)n2);
+        if (sa < 0 || sb < 0) return false;
+        int shs;
+        auto tabs = B.tw4(n, &shs);
+        for (int d = 0; d < 2; ++d) {
+            GStage a = base_stage(sa, (int)n2, lines_per_tile((int)n1, cfg.lpt_a), d);
+            a.in_buf = G_BUF_IN;
+            a.out_buf = G_BUF_W1;
+            a.in_line_fast = a.out_line_fast = 1;
+            a.in_ls = a.out_ls = 1;
+            a.in_es = a.out_es = n2;
+            a.in_valid = a.out_valid = n;
+            a.post = G_POST_TW4;
+            a.lo = tabs.first;
+            a.hi = tabs.second;
+            a.sh = shs;
+            GStage b = base_stage(sb, (int)n1, lines_per_tile((int)n2, cfg.lpt_b), d);
+            b.in_buf = G_BUF_W1;
+            b.out_buf = G_BUF_OUT;
+            b.out_line_fast = 1;
+            b.in_ls = n2;
+            b.in_es = 1;
+            b.out_ls = 1;
+            b.out_es = n1;
+            b.in_valid = b.out_valid = n;
+            (d ? i : f).push_back(a);
+            (d ? i : f).push_back(b);
+        }
+        *w1 = n;
+    } else {
+        // Bluestein: M = 2^k >= 2n - 1
+        const int64_t M = next_pow2(2 * n - 1);
+        auto bt = B.blue(n, M);
+        if (M <= cfg.tile_max) {
+            const int sm = B.shape((int)M);
+            for (int d = 0; d < 2; ++d) {
+                GStage a = base_stage(sm, 1, 1, 0);
+                a.in_buf = G_BUF_IN;
+                a.out_buf = G_BUF_W1;
+                a.in_ls = a.out_ls = M;
+                a.in_es = a.out_es = 1;
+                a.in_valid = n;
+                a.out_valid = M;
+                a.pre = d ? G_PRE_TABLE_CONJ : G_PRE_TABLE;
+                a.pre_tab = bt[0];
+                a.post = G_POST_TABLE;
+                a.post_tab = d ? bt[2] : bt[1];
+                GStage b = base_stage(sm, 1, 1, 1);
+                b.in_buf = G_BUF_W1;
+                b.out_buf = G_BUF_OUT;
+                b.in_ls = b.out_ls = M;
+                b.in_es = b.out_es = 1;
+                b.in_valid = M;
+                b.out_valid = n;
+                b.post = d ? G_POST_TABLE_CONJ : G_POST_TABLE;
+                b.post_tab = bt[0];
+                (d ? i : f).push_back(a);
+                (d ? i : f).push_back(b);
+            }
+            *w1 = M;
+        } else {
+            int64_t m1, m2;
+            if (!split_four(M, cfg.tile_max, 0, &m1, &m2)) return false;
+            const int sa = B.shape((int)m1), sb = B.shape((int)m2);
+            int shs;
+            auto tabs = B.tw4(M, &shs);
+            for (int d = 0; d < 2; ++d) {
+                for (int k = 0; k < 2; ++k) {  // k = 0: FFT_M of x*w; k = 1: IFFT_M
+                    GStage a = base_stage(sa, (int)m2, lines_per_tile((int)m1, cfg.lpt_a), k);
+                    a.in_buf = k ? G_BUF_W2 : G_BUF_IN;
+                    a.out_buf = G_BUF_W1;
+                    a.in_line_fast = a.out_line_fast = 1;
+                    a.in_ls = a.out_ls = 1;
+                    a.in_es = a.out_es = m2;
+                    a.in_valid = k ? M : n;
+                    a.out_valid = M;
+                    if (!k) {
+                        a.pre = d ? G_PRE_TABLE_CONJ : G_PRE_TABLE;
+                        a.pre_tab = bt[0];
+                    }
+                    a.post = G_POST_TW4;
+                    a.lo = tabs.first;
+                    a.hi = tabs.second;
+                    a.sh = shs;
+                    GStage b = base_stage(sb, (int)m1, lines_per_tile((int)m2, cfg.lpt_b), k);
+                    b.in_buf = G_BUF_W1;
+                    b.out_buf = k ? G_BUF_OUT : G_BUF_W2;
+                    b.out_line_fast = 1;
+                    b.in_ls = m2;
+                    b.in_es = 1;
+                    b.out_ls = 1;
+                    b.out_es = m1;
+                    b.in_valid = M;
+                    b.out_valid = k ? n : M;
+                    if (!k) {
+                        b.post = G_POST_TABLE;
+                        b.post_tab = d ? bt[2] : bt[1];
+                    } else {
+                        b.post = d ? G_POST_TABLE_CONJ : G_POST_TABLE;
+                        b.post_tab = bt[0];
+                    }
+                    (d ? i : f).push_back(a);
+                    (d ? i : f).push_back(b);
+                }
+            }
+            *w1 = M;
+            *w2 = M;
+        }
+    }
+    *nstages = (int)f.size();
+    B.st_f.insert(B.st_f.end(), f.begin(), f.end());
+    B.st_i.insert(B.st_i.end(), i.begin(), i.end());
+    return true;
+}
+
+template <class T>
+cudaError_t upload(T** d, const std::vector<T>& h) {
+    if (h.empty()) {
+        *d = nullptr;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(d, sizeof(T) * h.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+GExecArgs make_args(const GraphPlan* gp, const float2* in, float2* out, bool inv, int* d_status, int single,
+                    int item0) {
+    GExecArgs a{};
+    a.in = in;
+    a.out = out;
+    a.work = gp->work;
+    a.pool = gp->pool;
+    a.shapes = gp->shapes;
+    a.stages = gp->stages[inv ? 1 : 0];
+    a.xf = gp->xf;
+    a.items = gp->items;
+    a.nitems = gp->nitems;
+    a.ctl = gp->ctl;
+    a.status = d_status;
+    a.spin_limit = gp->spin_limit;
+    a.single = single;
+    a.item0 = item0;
+    return a;
+}
+
+}  // namespace
+
+bool graph_length_supported(int64_t n) {
+    if (n < 1) return false;
+    if (is_smooth(n)) return n <= (int64_t)kGTileMax * kGTileMax;
+    return next_pow2(2 * n - 1) <= (int64_t)kGTileMax * kGTileMax;
+}
+
+fft_status graph_plan_build(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_t batch, bool ragged) {
+    Builder B;
+    GLenConfig cfg;
+    cfg.tile_max = env_i("B300FFT_G_TILE_MAX", kGTileMax);
+    if (cfg.tile_max > kGTileMax || cfg.tile_max < 16) cfg.tile_max = kGTileMax;
+    cfg.lpt_a = env_i("B300FFT_G_LPT_A", 0);
+    cfg.lpt_b = env_i("B300FFT_G_LPT_B", 0);
+    for (int64_t n : lengths)
+        if (!graph_length_supported(n)) return FFT_ERR_UNSUPPORTED;
+
+    // kinds: distinct lengths, largest first (big work dequeued early)
+    std::vector<int64_t> uniq(lengths.begin(), lengths.end());
+    std::sort(uniq.begin(), uniq.end(), std::greater<int64_t>());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    struct Kind {
+        int first, nstages;
+        int64_t w1, w2;
+        int64_t lines;
+    };
+    std::map<int64_t, Kind> kinds;
+    const bool uniform = !ragged;
+    for (int64_t n : uniq) {
+        Kind k{};
+        k.first = (int)B.st_f.size();
+        const bool single_tile = is_smooth(n) && n <= cfg.tile_max;
+        k.lines = (uniform && single_tile) ? batch : 1;
+        if (k.lines > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+        if (!build_kind(B, n, k.lines, cfg, &k.nstages, &k.w1, &k.w2)) return FFT_ERR_UNSUPPORTED;
+        kinds[n] = k;
+    }
+
+    // transforms (packed offsets), workspace, counters
+    std::vector<GTransform> xf;
+    int64_t off = 0, woff = 0;
+    int ctr = 0;
+    auto add_xf = [&](int64_t n, int64_t at) {
+        const Kind& k = kinds[n];
+        GTransform x{};
+        x.kind = k.first;
+        x.nstages = k.nstages;
+        x.ctr = ctr;
+        ctr += k.nstages - 1;
+        x.in_off = x.out_off = at;
+        x.w1_off = woff;
+        woff += (k.w1 + 1) & ~int64_t(1);
+        x.w2_off = woff;
+        woff += (k.w2 + 1) & ~int64_t(1);
+        xf.push_back(x);
+    };
+    if (ragged) {
+        for (int64_t n : lengths) {
+            add_xf(n, off);
+            off += n;
+        }
+    } else {
+        const int64_t n = lengths[0];
+        if (kinds[n].lines > 1) add_xf(n, 0);
+        else
+            for (int64_t b = 0; b < batch; ++b) add_xf(n, b * n);
+    }
+    if ((int64_t)xf.size() >= (int64_t(1) << 31)) return FFT_ERR_UNSUPPORTED;
+
+    // queue: stage rounds; within a round, kinds largest first
+    std::vector<uint64_t> items;
+    int maxst = 0;
+    for (auto& kv : kinds) maxst = std::max(maxst, kv.second.nstages);
+    std::vector<std::vector<int>> by_kind;  // transform indices per kind, kinds in uniq order
+    for (int64_t n : uniq) {
+        std::vector<int> v;
+        for (int t = 0; t < (int)xf.size(); ++t)
+            if (xf[t].kind == kinds[n].first) v.push_back(t);
+        by_kind.push_back(v);
+    }
+    gp->groups.clear();
+    for (int s = 0; s < maxst; ++s) {
+        for (size_t ki = 0; ki < uniq.size(); ++ki) {
+            const Kind& k = kinds[uniq[ki]];
+            if (s >= k.nstages) continue;
+            const GStage& st = B.st_f[k.first + s];
+            const int g0 = (int)items.size();
+            for (int t : by_kind[ki])
+                for (int tile = 0; tile < st.ntiles; ++tile)
+                    items.push_back(((uint64_t)t << 32) | ((uint64_t)s << 24) | (uint64_t)tile);
+            if ((int)items.size() > g0) gp->groups.push_back({g0, (int)items.size()});
+        }
+    }
+    if (items.size() >= (size_t)0x7fffffff) return FFT_ERR_UNSUPPORTED;
+
+    // device data
+    cudaStream_t st = 0;
+    if (cudaMalloc(&gp->pool, sizeof(float2) * (size_t)std::max<int64_t>(B.pool_size, 2)) != cudaSuccess)
+        return FFT_ERR_ALLOC;
+    for (auto& t : B.pass_tabs)
+        if (gen_pass_table(gp->pool + t.off, t.ns, t.r, st) != cudaSuccess) return FFT_ERR_CUDA;
+    for (auto& t : B.root_tabs)
+        if (gen_root_table(gp->pool + t.off, t.count, t.mult, t.n, st) != cudaSuccess) return FFT_ERR_CUDA;
+    if (!B.blue_list.empty()) {
+        int64_t maxM = 0;
+        for (auto& b : B.blue_list) maxM = std::max(maxM, b.M);
+        double2* scratch = nullptr;
+        if (cudaMalloc(&scratch, sizeof(double2) * 2 * (size_t)maxM) != cudaSuccess) return FFT_ERR_ALLOC;
+        cudaError_t e = cudaSuccess;
+        for (auto& b : B.blue_list) {
+            if (e == cudaSuccess) e = gen_chirp(gp->pool + b.chirp, b.n, st);
+            if (e == cudaSuccess) e = gen_bluestein_filter(gp->pool + b.ff, b.n, b.M, false, scratch, st);
+            if (e == cudaSuccess) e = gen_bluestein_filter(gp->pool + b.fi, b.n, b.M, true, scratch, st);
+        }
+        cudaDeviceSynchronize();
+        cudaFree(scratch);
+        if (e != cudaSuccess) return FFT_ERR_CUDA;
+    }
+    if (upload(&gp->shapes, B.shapes) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (upload(&gp->stages[0], B.st_f) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (upload(&gp->stages[1], B.st_i) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (upload(&gp->xf, xf) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (upload(&gp->items, items) != cudaSuccess) return FFT_ERR_ALLOC;
+    gp->nitems = (int)items.size();
+    gp->ncounters = ctr;
+    gp->ntransforms = (int)xf.size();
+    if (cudaMalloc(&gp->ctl, sizeof(int) * (size_t)(1 + ctr)) != cudaSuccess) return FFT_ERR_ALLOC;
+    gp->work_bytes = (size_t)woff * sizeof(float2);
+    if (woff > 0 && cudaMalloc(&gp->work, gp->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (cudaFuncSetAttribute(k_gexec, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    int bps = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_gexec, kGThreads, kGSmem) != cudaSuccess || bps < 1)
+        return FFT_ERR_CUDA;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    gp->grid = std::max(1, std::min(gp->nitems, sms * bps));
+    gp->spin_limit = env_i("B300FFT_SPIN_LIMIT", 1 << 23);
+    gp->use_graph = env_i("B300FFT_GRAPH", 1) != 0;
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "graph kinds=%zu transforms=%d items=%d stages<=%d grid=%d work=%zuB pool=%lldB",
+                  uniq.size(), gp->ntransforms, gp->nitems, maxst, gp->grid, gp->work_bytes,
+                  (long long)(B.pool_size * 8));
+    gp->desc = buf;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
+    return FFT_OK;
+}
+
+void graph_plan_free(GraphPlan* gp) {
+    for (int d = 0; d < 2; ++d) {
+        if (gp->gexec[d]) cudaGraphExecDestroy(gp->gexec[d]);
+        if (gp->graph[d]) cudaGraphDestroy(gp->graph[d]);
+        if (gp->stages[d]) cudaFree(gp->stages[d]);
+        gp->gexec[d] = nullptr;
+        gp->graph[d] = nullptr;
+        gp->stages[d] = nullptr;
+    }
+    cudaFree(gp->pool);
+    cudaFree(gp->shapes);
+    cudaFree(gp->xf);
+    cudaFree(gp->items);
+    cudaFree(gp->ctl);
+    cudaFree(gp->work);
+    gp->pool = nullptr;
+    gp->shapes = nullptr;
+    gp->xf = nullptr;
+    gp->items = nullptr;
+    gp->ctl = nullptr;
+    gp->work = nullptr;
+}
+
+namespace {
+// Capture memset(ctl) + the persistent launch once per direction; later
+// execs only patch the in/out pointers of the kernel node.
+cudaError_t ensure_graph(GraphPlan* gp, bool inv, const GExecArgs& a) {
+    const int d = inv ? 1 : 0;
+    if (gp->gexec[d]) return cudaSuccess;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(1 + gp->ncounters), cs);
+        k_gexec<<<gp->grid, kGThreads, kGSmem, cs>>>(a);
+        e = cudaStreamEndCapture(cs, &gp->graph[d]);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return e;
+    size_t nn = 0;
+    cudaGraphGetNodes(gp->graph[d], nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(gp->graph[d], nodes.data(), &nn);
+    for (auto n : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(n, &t);
+        if (t == cudaGraphNodeTypeKernel) gp->knode[d] = n;
+    }
+    if (!gp->knode[d]) return cudaErrorUnknown;
+    return cudaGraphInstantiate(&gp->gexec[d], gp->graph[d], 0);
+}
+}  // namespace
+
+fft_status graph_plan_exec(GraphPlan* gp, const float2* in, float2* out, bool inv, cudaStream_t st, int* d_status,
+                           bool per_stage) {
+    cudaError_t e = cudaSuccess;
+    if (per_stage) {
+        for (auto& g : gp->groups) {
+            GExecArgs a = make_args(gp, in, out, inv, d_status, 1, g.first);
+            k_gexec<<<g.second - g.first, kGThreads, kGSmem, st>>>(a);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return FFT_ERR_CUDA;
+        }
+        return FFT_OK;
+    }
+    GExecArgs a = make_args(gp, in, out, inv, d_status, 0, 0);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    if (gp->use_graph && cap == cudaStreamCaptureStatusNone) {
+        const int d = inv ? 1 : 0;
+        if (ensure_graph(gp, inv, a) != cudaSuccess) return FFT_ERR_CUDA;
+        cudaKernelNodeParams kp{};
+        void* params[1] = {&a};
+        kp.func = (void*)k_gexec;
+        kp.gridDim = dim3(gp->grid);
+        kp.blockDim = dim3(kGThreads);
+        kp.sharedMemBytes = kGSmem;
+        kp.kernelParams = params;
+        e = cudaGraphExecKernelNodeSetParams(gp->gexec[d], gp->knode[d], &kp);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gp->gexec[d], st);
+        return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+    }
+    e = cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(1 + gp->ncounters), st);
+    if (e == cudaSuccess) {
+        k_gexec<<<gp->grid, kGThreads, kGSmem, st>>>(a);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
+}
+
+}  // namespace b300fft

@@ -18,6 +18,13 @@ int pow2_table_entries(int logn);
 cudaError_t gen_pow2_table(float2* tw, int logn, cudaStream_t st);
 // out[i] = W_n^((i * mult) mod n) = exp(-2 pi i (i*mult mod n)/n), i < count.
 cudaError_t gen_root_table(float2* out, int64_t count, int64_t mult, int64_t n, cudaStream_t st);
+// One Stockham pass block: out[(r-1)*Ns + k] = W_{Ns*R}^{k*r}, r < R, k < Ns.
+cudaError_t gen_pass_table(float2* out, int Ns, int R, cudaStream_t st);
+// Bluestein chirp w[n] = exp(-pi i (n^2 mod 2N)/N), n < N.
+cudaError_t gen_chirp(float2* out, int64_t n, cudaStream_t st);
+// Bluestein filter FFT_M(b)/M (FP64, rounded once); scratch = 2*M double2.
+cudaError_t gen_bluestein_filter(float2* out, int64_t n, int64_t M, bool inverse, double2* scratch,
+                                 cudaStream_t st);
 
 // --- rows kernel (k_rows.cu) ----------------------------------------------
 // nrows contiguous transforms of length 2^logn, [nrows][2^logn] -> same layout.

@@ -21,9 +21,8 @@ enum class PlanKind : int {
     TensorCore // radix-16 stages as tensor-core GEMMs
 };
 
-struct GenericPlan;   // generic.cu
-struct RaggedPlan;    // ragged.cu
-struct TcPlan;        // tc.cu
+struct GraphPlan;  // gplan.h
+struct TcPlan;     // tc.cu
 
 }  // namespace b300fft
 
@@ -59,8 +58,7 @@ struct fft_plan_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
 
-    b300fft::GenericPlan* generic = nullptr;
-    b300fft::RaggedPlan* ragged = nullptr;
+    b300fft::GraphPlan* gplan = nullptr;  // Generic / Ragged kinds
     b300fft::TcPlan* tc = nullptr;
 
     int kernels = 0;
@@ -71,11 +69,13 @@ namespace b300fft {
 
 void destroy_plan_resources(fft_plan_s* p);
 // only < 0: every kernel; else only kernel `only` of the sequence
-fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only = -1);
+fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only = -1,
+                     bool per_size = false);
 
 // Builders of the other kernel families (return FFT_ERR_UNSUPPORTED when the
 // shape is outside what they implement).
 fft_status build_generic_1d(fft_plan_s* p);
+fft_status build_ragged(fft_plan_s* p, const int64_t* lengths, int64_t count);
 fft_status build_tc_plan(fft_plan_s* p);
 
 }  // namespace b300fft

@@ -93,3 +93,90 @@ cudaError_t gen_root_table(float2* out, int64_t count, int64_t mult, int64_t n, 
 }
 
 }  // namespace b300fft
+
+// ---------------------------------------------------------------------------
+// Tables of the generic (mixed-radix) passes and of Bluestein's algorithm.
+// ---------------------------------------------------------------------------
+namespace b300fft {
+
+cudaError_t gen_pass_table(float2* out, int Ns, int R, cudaStream_t st) {
+    const int cnt = (R - 1) * Ns;
+    if (cnt <= 0) return cudaSuccess;
+    k_tw_pass<<<(cnt + 255) / 256, 256, 0, st>>>(out, Ns, R);
+    return cudaGetLastError();
+}
+
+// Bluestein chirp w[n] = exp(-pi i (n^2 mod 2N) / N), n < N, the index
+// reduced exactly in 64-bit integers before the FP64 evaluation.
+__global__ void k_chirp(float2* out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t m = (int64_t)(((__int128)i * i) % (2 * n));
+    double s, c;
+    sincospi((double)m / (double)n, &s, &c);
+    out[i] = make_float2((float)c, (float)(-s));
+}
+
+// Bluestein kernel sequence b of length M (FP64): b[m] = exp(sg*pi i (m^2 mod
+// 2N)/N) for m < N and b[M-m] = b[m] for 0 < m < N, zero elsewhere.  With
+// sg = +1 this is conj(w) (forward transform), with sg = -1 it is w (inverse).
+__global__ void k_bluestein_seq(double2* b, int64_t n, int64_t M, int sg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int64_t m = -1;
+    if (i < n) m = i;
+    else if (i > M - n) m = M - i;
+    double2 v = make_double2(0.0, 0.0);
+    if (m >= 0) {
+        const int64_t q = (int64_t)(((__int128)m * m) % (2 * n));
+        double s, c;
+        sincospi((double)q / (double)n, &s, &c);
+        v = make_double2(c, sg * s);
+    }
+    b[i] = v;
+}
+
+// One radix-2 Stockham pass in FP64 (forward), plan time only.
+__global__ void k_fp64_radix2(const double2* __restrict__ src, double2* __restrict__ dst, int64_t M, int64_t Ns) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M / 2) return;
+    const int64_t k = j % Ns;
+    double s, c;
+    sincospi(-(double)k / (double)Ns, &s, &c);  // W_{2Ns}^k
+    const double2 a = src[j], b0 = src[j + M / 2];
+    const double2 b = make_double2(b0.x * c - b0.y * s, b0.x * s + b0.y * c);
+    const int64_t d = (j / Ns) * 2 * Ns + k;
+    dst[d] = make_double2(a.x + b.x, a.y + b.y);
+    dst[d + Ns] = make_double2(a.x - b.x, a.y - b.y);
+}
+
+__global__ void k_round_scale(const double2* __restrict__ src, float2* __restrict__ out, int64_t M, double scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    out[i] = make_float2((float)(src[i].x * scale), (float)(src[i].y * scale));
+}
+
+cudaError_t gen_chirp(float2* out, int64_t n, cudaStream_t st) {
+    k_chirp<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n);
+    return cudaGetLastError();
+}
+
+// out[0..M) = FFT_M(b)/M in FP64, rounded once to FP32 (the Bluestein filter).
+// scratch: 2*M double2 of device memory.
+cudaError_t gen_bluestein_filter(float2* out, int64_t n, int64_t M, bool inverse, double2* scratch,
+                                 cudaStream_t st) {
+    double2* a = scratch;
+    double2* b = scratch + M;
+    const unsigned g = (unsigned)((M + 255) / 256);
+    k_bluestein_seq<<<g, 256, 0, st>>>(a, n, M, inverse ? -1 : +1);
+    for (int64_t ns = 1; ns < M; ns *= 2) {
+        k_fp64_radix2<<<(unsigned)((M / 2 + 255) / 256), 256, 0, st>>>(a, b, M, ns);
+        double2* t = a;
+        a = b;
+        b = t;
+    }
+    k_round_scale<<<g, 256, 0, st>>>(a, out, M, 1.0 / (double)M);
+    return cudaGetLastError();
+}
+
+}  // namespace b300fft

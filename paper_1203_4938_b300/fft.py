@@ -41,7 +41,7 @@ PRECISIONS = {"fp32": FFT_FP32, "tc_fp16": FFT_TC_FP16, "tc_bf16": FFT_TC_BF16,
 # Symbols declared in include/fft.h (checked by the CPU test-suite).
 EXPORTS = ("fft_plan_create", "fft_plan_create_ragged", "fft_last_error", "fft_exec",
            "fft_plan_check", "fft_plan_destroy", "fft_plan_workspace_bytes", "fft_status_string",
-           "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel")
+           "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size")
 
 _lock = threading.Lock()
 _lib = None
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fft_status_string.restype = ctypes.c_char_p
         lib.fft_plan_kernel_count.argtypes = [vp]
         lib.fft_plan_kernel_count.restype = ctypes.c_int
+        lib.fft_exec_per_size.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        lib.fft_exec_per_size.restype = ctypes.c_int
         lib.fft_exec_kernel.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]
         lib.fft_exec_kernel.restype = ctypes.c_int
         lib.fft_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
@@ -116,6 +118,10 @@ def fft_last_error() -> int:
 
 def fft_exec(plan, in_ptr: int, out_ptr: int, direction: int, stream: int = 0) -> int:
     return int(load().fft_exec(plan, in_ptr, out_ptr, int(direction), stream or None))
+
+
+def fft_exec_per_size(plan, in_ptr: int, out_ptr: int, direction: int, stream: int = 0) -> int:
+    return int(load().fft_exec_per_size(plan, in_ptr, out_ptr, int(direction), stream or None))
 
 
 def fft_exec_kernel(plan, k: int, in_ptr: int, out_ptr: int, direction: int, stream: int = 0) -> int:
@@ -194,6 +200,19 @@ class Plan:
         rc = fft_exec(self.handle, x.data_ptr(), out.data_ptr(), direction, s.cuda_stream)
         if rc != FFT_OK:
             raise FFTError(rc, "fft_exec")
+        return out
+
+    def exec_per_size(self, x, out=None, direction: int = FFT_FORWARD, stream=None):
+        """fft_exec_per_size: one launch per (stage, length) group (baseline form)."""
+        import torch
+        _check_tensor(x, self.numel, "input")
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.complex64, device=x.device)
+        _check_tensor(out, self.numel, "output")
+        s = stream if stream is not None else torch.cuda.current_stream(x.device)
+        rc = fft_exec_per_size(self.handle, x.data_ptr(), out.data_ptr(), direction, s.cuda_stream)
+        if rc != FFT_OK:
+            raise FFTError(rc, "fft_exec_per_size")
         return out
 
     def exec_kernel(self, k: int, x, out, direction: int = FFT_FORWARD, stream=None):

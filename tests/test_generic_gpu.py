@@ -1,0 +1,130 @@
+"""Parity of the mixed-radix, Bluestein and ragged paths with the FP64 oracle
+(needs a GPU).  Bar: per-transform relative L2 error <= 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_4938_b300 import inputs
+from tests.gpu_util import TOL_FP32, cuda_or_skip, max_rel_l2, run, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+def ref_bins(x, sign, nbins=48, seed=0):
+    """Oracle for one long transform: selected bins only (O(N) each)."""
+    n = x.shape[-1]
+    ks = np.unique(np.concatenate([[0, 1, n - 1, n // 2],
+                                   np.random.default_rng(seed).integers(0, n, nbins)]))
+    return ks, oracle.dft_bins(x, ks, sign)
+
+
+def bins_rel_err(y, ks, vals):
+    return float(np.linalg.norm(y[ks] - vals) / np.linalg.norm(vals))
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 6, 7, 9, 12, 15, 21, 25, 35, 48, 49, 80, 96, 112, 320, 448, 768,
+                               1000, 1536, 2560, 3072, 3584, 4000, 4032])
+@pytest.mark.parametrize("batch", [1, 7])
+def test_mixed_radix_single_tile(torch, n, batch):
+    x = inputs.uniform_batch(batch, n, seed=n + batch)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d)
+        assert max_rel_l2(y, oracle.fft(x, d), -1) <= TOL_FP32, (n, batch, d)
+
+
+@pytest.mark.parametrize("n", [3 * 2 ** 12, 5 * 2 ** 12, 7 * 2 ** 13, 3 * 2 ** 14, 3 ** 9, 5 ** 6, 6000, 7 * 2 ** 16])
+def test_mixed_radix_four_step(torch, n):
+    batch = 2
+    x = inputs.normal_batch(batch, n, seed=n % 1000)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d)
+        assert max_rel_l2(y, oracle.fft(x, d), -1) <= TOL_FP32, (n, d)
+
+
+@pytest.mark.parametrize("n", [11, 13, 22, 97, 101, 143, 1009, 2003, 2053, 4099])
+def test_bluestein(torch, n):
+    batch = 3
+    x = inputs.uniform_batch(batch, n, seed=n)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d)
+        ref = oracle.dft_naive(x, d)
+        assert max_rel_l2(y, ref, -1) <= TOL_FP32, (n, d)
+
+
+@pytest.mark.parametrize("n", [30011, 65521])
+def test_bluestein_large_sampled(torch, n):
+    x = inputs.uniform_batch(1, n, seed=n)
+    for d in (-1, +1):
+        y = run((n,), 1, x, d)[0]
+        ks, vals = ref_bins(x[0], d)
+        assert bins_rel_err(y, ks, vals) <= TOL_FP32, (n, d)
+        # whole-transform property check: Parseval
+        e_in = np.sum(np.abs(x[0].astype(np.complex128)) ** 2)
+        e_out = np.sum(np.abs(y.astype(np.complex128)) ** 2)
+        assert abs(e_out - n * e_in) <= 4 * TOL_FP32 * n * e_in
+
+
+def _ragged_check(torch, lengths, data, per_size, d, full_limit=20000):
+    from paper_1203_4938_b300 import fft as F
+    offs = np.zeros(len(lengths) + 1, np.int64)
+    np.cumsum(lengths, out=offs[1:])
+    with F.Ragged(lengths) as p:
+        xd = to_dev(data)
+        y = (p.exec_per_size(xd, None, d) if per_size else p.exec(xd, None, d))
+        torch.cuda.synchronize()
+        p.check()
+        yh = y.cpu().numpy()
+    worst = 0.0
+    for t, n in enumerate(lengths):
+        xs, ys = data[offs[t]:offs[t + 1]], yh[offs[t]:offs[t + 1]]
+        if n <= full_limit:
+            e = max_rel_l2(ys[None], oracle.fft(xs[None], d), -1)
+        else:
+            ks, vals = ref_bins(xs, d, nbins=16, seed=t)
+            e = bins_rel_err(ys, ks, vals)
+        worst = max(worst, e)
+    return worst
+
+
+@pytest.mark.parametrize("per_size", [False, True])
+def test_ragged_small_mix(torch, per_size):
+    lengths, _ = inputs.ragged_lengths(count=160, seed=11)
+    lengths = [int(v) for v in lengths]
+    data = np.random.default_rng(3).uniform(-1, 1, 2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    for d in (-1, +1):
+        assert _ragged_check(torch, lengths, data, per_size, d) <= TOL_FP32
+
+
+def test_ragged_edge_lengths(torch):
+    lengths = [1, 2, 3, 4096, 4097, 17, 65536, 64, 5, 7 * 2 ** 13, 1, 2053]
+    data = np.random.default_rng(5).standard_normal(2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    for per_size in (False, True):
+        assert _ragged_check(torch, lengths, data, per_size, -1) <= TOL_FP32
+
+
+def test_ragged_graph_capture_by_caller(torch):
+    """fft_exec inside the caller's stream capture launches the persistent
+    kernel directly (not the plan's own graph) and replays correctly."""
+    from paper_1203_4938_b300 import fft as F
+    lengths = [64, 96, 1000, 4096, 12288, 131]
+    data = np.random.default_rng(6).uniform(-1, 1, 2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    ref = np.concatenate([oracle.fft(data[a:a + n], -1) for a, n in
+                          zip(np.concatenate([[0], np.cumsum(lengths)[:-1]]), lengths)])
+    with F.Ragged(lengths) as p:
+        xd = to_dev(data)
+        out = torch.empty_like(xd)
+        p.exec(xd, out)  # first exec outside capture builds the plan's graph
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        out2 = torch.empty_like(xd)
+        with torch.cuda.graph(g):
+            p.exec(xd, out2)
+        g.replay()
+        g.replay()
+        torch.cuda.synchronize()
+        assert max_rel_l2(out2.cpu().numpy()[None], ref[None], -1) <= TOL_FP32
