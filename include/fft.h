@@ -134,6 +134,32 @@ FFT_API int fft_plan_kernel_count(fft_plan plan);
  * exactly fft_exec.  For per-kernel timing and profiling. */
 FFT_API fft_status fft_exec_kernel(fft_plan plan, int k, const void *in, void *out, int direction, void *stream);
 
+/* Allocation-free 1-D transform.  The paper has no counterpart to this entry
+ * point; it exists for callers that cannot call cudaMalloc -- code that runs
+ * after its host has fixed every device allocation (an embedded engine, a
+ * plugin whose host forbids allocation, a loop that budgets all device memory
+ * at start-up) -- and so cannot create a plan, whose tables and workspace are
+ * allocated.  It computes the same transform as a plan for (1, {n}, batch)
+ * with the same two-pass kernels, but keeps its workspace and twiddle tables
+ * in arrays that are part of the library image: every GPU that loads the
+ * library holds them (about 32.1 MiB) until the process exits.
+ *   in, out    device pointers, 16-byte aligned, batch * n complex64 each
+ *              ([batch][n]); in == out is allowed.
+ *   n          a power of two, 2^13 <= n <= 2^22.
+ *   batch      >= 1 with n * batch <= 2^22 (the size of the static
+ *              workspace); larger requests return FFT_ERR_INVALID_ARG.
+ *   direction  FFT_FORWARD or FFT_INVERSE;  stream  a cudaStream_t or NULL.
+ * Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * The first call on a device looks up the device addresses of the static
+ * arrays and sets kernel attributes for that device; make that first call
+ * before any stream capture.  Every call on a device shares the same arrays
+ * (the tables are rebuilt on the stream by each call, the workspace is fully
+ * overwritten before it is read), so calls whose execution overlaps on the
+ * GPU -- on different streams, or from different threads -- race and give
+ * wrong results; order them on one stream.  Asynchronous like fft_exec. */
+FFT_API fft_status fft_exec_pow2_static(const void *in, void *out, int64_t n, int64_t batch, int direction,
+                                        void *stream);
+
 /* Human-readable one-line description of the plan's decomposition (kernel
  * family, radix sequence, tile shape) copied into buf (NUL-terminated,
  * truncated to cap bytes).  Returns the full length, or -1 on a bad handle. */

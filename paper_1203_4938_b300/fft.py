@@ -41,7 +41,8 @@ PRECISIONS = {"fp32": FFT_FP32, "tc_fp16": FFT_TC_FP16, "tc_bf16": FFT_TC_BF16,
 # Symbols declared in include/fft.h (checked by the CPU test-suite).
 EXPORTS = ("fft_plan_create", "fft_plan_create_ragged", "fft_last_error", "fft_exec",
            "fft_plan_check", "fft_plan_destroy", "fft_plan_workspace_bytes", "fft_status_string",
-           "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size")
+           "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size",
+           "fft_exec_pow2_static")
 
 _lock = threading.Lock()
 _lib = None
@@ -83,6 +84,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fft_status_string.restype = ctypes.c_char_p
         lib.fft_plan_kernel_count.argtypes = [vp]
         lib.fft_plan_kernel_count.restype = ctypes.c_int
+        lib.fft_exec_pow2_static.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, vp]
+        lib.fft_exec_pow2_static.restype = ctypes.c_int
         lib.fft_exec_per_size.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         lib.fft_exec_per_size.restype = ctypes.c_int
         lib.fft_exec_kernel.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]
@@ -118,6 +121,12 @@ def fft_last_error() -> int:
 
 def fft_exec(plan, in_ptr: int, out_ptr: int, direction: int, stream: int = 0) -> int:
     return int(load().fft_exec(plan, in_ptr, out_ptr, int(direction), stream or None))
+
+
+def fft_exec_pow2_static(in_ptr: int, out_ptr: int, n: int, batch: int, direction: int, stream: int = 0) -> int:
+    """Allocation-free transform of batch x n (power of two, 2^13..2^22,
+    n*batch <= 2^22) using the library's static workspace; see include/fft.h."""
+    return int(load().fft_exec_pow2_static(in_ptr, out_ptr, int(n), int(batch), int(direction), stream or None))
 
 
 def fft_exec_per_size(plan, in_ptr: int, out_ptr: int, direction: int, stream: int = 0) -> int:
