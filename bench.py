@@ -388,9 +388,41 @@ def run_image2d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """Precision forms: batch 4096 x N=4096 and 256 x N=65536, normal(0,1)
+    seed 3; FP32 Stockham vs tensor-core radix-16 (FP16/BF16, hi+lo and
+    plain), forward; time and relative L2 error against the FP64 oracle on
+    sampled transforms."""
+    import torch
+    import oracle
+    from paper_1203_4938_b300 import build as B
+    from paper_1203_4938_b300 import fft as F
+    B.build()
+    parts = {}
+    for n, bt in ((4096, 4096), (65536, 256)):
+        xh = inputs.normal_batch(bt, n, seed=3)
+        x = torch.from_numpy(xh).cuda()
+        y = torch.empty_like(x)
+        sample = [0, bt // 2, bt - 1]
+        ref = oracle.fft(xh[sample], -1)
+        for mode in ("fp32", "tc_fp16", "tc_bf16", "tc_fp16_plain", "tc_bf16_plain"):
+            p = F.Plan((n,), bt, mode)
+            ms = _time_stream(lambda: p.forward(x, y), args.steps, args.warmup)
+            yh = y[sample].cpu().numpy()
+            d = np.sqrt(np.sum(np.abs(yh - ref) ** 2, -1)) / np.sqrt(np.sum(np.abs(ref) ** 2, -1))
+            parts[f"{bt}x{n} {mode}"] = {"us": ms * 1e3, "gflops": bt * 5.0 * n * math.log2(n) / (ms * 1e-3) / 1e9,
+                                         "effective_gbs": 16.0 * bt * n / (ms * 1e-3) / 1e9,
+                                         "rel_l2_max": float(d.max()), "plan": p.describe()}
+            p.close()
+    line = {"metric": "precision forms: us per forward exec and rel-L2 vs FP64 oracle", "unit": "us",
+            "config": {"workload": "4096x4096 and 256x65536, normal(0,1) seed 3"}, "parts": parts,
+            "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ragged", "image2d"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ragged", "image2d", "precision"])
     ap.add_argument("--count", type=int, default=10000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -408,6 +440,8 @@ def main():
         run_ragged(args)
     elif args.workload == "image2d":
         run_image2d(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_gpu(args)
 

@@ -57,6 +57,8 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                                 nullptr, nullptr, 0, st);
             break;
         }
+        case PlanKind::TensorCore:
+            return exec_tc(p, in, out, inv, st, only);
         case PlanKind::Generic:
         case PlanKind::Ragged:
             if (!want(0)) return FFT_OK;
@@ -67,6 +69,5 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
     return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
 }
 
-fft_status build_tc_plan(fft_plan_s*) { return FFT_ERR_UNSUPPORTED; }
 
 }  // namespace b300fft

@@ -77,5 +77,6 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
 fft_status build_generic_1d(fft_plan_s* p);
 fft_status build_ragged(fft_plan_s* p, const int64_t* lengths, int64_t count);
 fft_status build_tc_plan(fft_plan_s* p);
+fft_status exec_tc(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only);
 
 }  // namespace b300fft

@@ -1,0 +1,57 @@
+"""Tensor-core radix-16 path (tcgen05, FP16/BF16 operands, FP32 accumulation)
+against the FP64 oracle (needs a GPU).
+
+Stated tolerances (per-transform relative L2, max over the batch), from the
+operand precision: a hi+lo split keeps ~22 bits (FP16) or ~16 bits (BF16) of
+each product, the plain forms 11 and 8 bits, with errors growing slowly with
+the number of radix-16 passes:
+    fp16 hi+lo 1e-6   bf16 hi+lo 2e-5   fp16 plain 2e-3   bf16 plain 2e-2
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_4938_b300 import inputs
+from tests.gpu_util import cuda_or_skip, max_rel_l2, run
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"tc_fp16": 1e-6, "tc_bf16": 2e-5, "tc_fp16_plain": 2e-3, "tc_bf16_plain": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.mark.parametrize("mode", list(TOL))
+@pytest.mark.parametrize("n,batch", [(256, 37), (4096, 5), (65536, 3)])
+def test_tc_parity(torch, mode, n, batch):
+    x = inputs.normal_batch(batch, n, seed=n + batch)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d, precision=mode)
+        err = max_rel_l2(y, oracle.fft(x, d), -1)
+        assert err <= TOL[mode], (mode, n, d, err)
+
+
+@pytest.mark.parametrize("mode", ["tc_fp16", "tc_bf16"])
+def test_tc_dynamic_range(torch, mode):
+    """Per-butterfly power-of-two scaling: a large constant offset (DC of
+    N * 1e4) and tiny inputs (1e-30) keep the relative error of the split."""
+    n = 4096
+    base = inputs.normal_batch(2, n, seed=9)
+    for x in (base + np.complex64(1e4), base * np.float32(1e-30)):
+        y = run((n,), 2, x.astype(np.complex64), -1, precision=mode)
+        err = max_rel_l2(y, oracle.fft(x, -1), -1)
+        assert err <= TOL[mode], (mode, err)
+
+
+def test_tc_impulse_and_unsupported(torch):
+    from paper_1203_4938_b300 import fft as F
+    x = np.zeros((3, 4096), np.complex64)
+    x[:, 0] = 1
+    y = run((4096,), 3, x, -1, precision="tc_fp16")
+    assert np.allclose(y, 1, atol=1e-6)
+    for n in (64, 1024, 1 << 20, 3000):
+        assert F.fft_plan_create(1, [n], 1, F.FFT_TC_FP16) is None
+        assert F.fft_last_error() == F.FFT_ERR_UNSUPPORTED
