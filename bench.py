@@ -333,7 +333,12 @@ def run_ragged(args):
     B.build()
     lengths, offsets, data = inputs.ragged_workload(args.count, seed=4)
     lens = [int(v) for v in lengths]
+    if not args.no_tune:
+        os.environ["FFT_AUTOTUNE"] = "1"  # measured tile shapes per length
+    t0 = time.perf_counter()
     p = F.Ragged(lens)
+    plan_s = time.perf_counter() - t0
+    os.environ.pop("FFT_AUTOTUNE", None)
     x = torch.from_numpy(data).cuda()
     y = torch.empty_like(x)
     fl = sum(5.0 * n * math.log2(n) for n in lens if n > 1)
@@ -344,7 +349,8 @@ def run_ragged(args):
             "value": fl / (ms_p * 1e-3) / 1e9, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_p, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"workload": f"ragged count={args.count} seed 4, forward",
-                                            "elements": int(offsets[-1]), "plan": p.describe()},
+                                            "elements": int(offsets[-1]), "plan": p.describe(),
+                                            "autotuned": not args.no_tune, "plan_seconds": plan_s},
             "per_size_launches": {"value": fl / (ms_s * 1e-3) / 1e9, "ms_per_step": ms_s},
             "persistent_over_per_size": ms_s / ms_p,
             "effective_gbs": 16.0 * offsets[-1] / (ms_p * 1e-3) / 1e9}
@@ -420,9 +426,39 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """One plan run `steps` times (the small cases profiled with ncu):
+    --case 1d|2d|ragged, --n (length, 2-D side, or ragged count), --batch,
+    --precision.  Input: normal(0,1) complex64 from torch's generator (1d,
+    2d) or the ragged workload (seed 4)."""
+    import torch
+    from paper_1203_4938_b300 import build as B
+    from paper_1203_4938_b300 import fft as F
+    B.build()
+    if args.case == "ragged":
+        lengths, _, data = inputs.ragged_workload(args.n, seed=4)
+        p = F.Ragged([int(v) for v in lengths])
+        x = torch.from_numpy(data).cuda()
+    else:
+        shape = (args.n, args.n) if args.case == "2d" else (args.n,)
+        p = F.Plan(shape, args.batch, args.precision)
+        x = torch.randn(p.shape, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    ms = _time_stream(lambda: p.forward(x, y), max(1, args.steps), args.warmup)
+    p.check()
+    print(json.dumps({"case": args.case, "n": args.n, "batch": args.batch, "precision": args.precision,
+                      "plan": p.describe(), "ms_per_exec": ms,
+                      "effective_gbs": 16.0 * x.numel() / (ms * 1e-3) / 1e9}), flush=True)
+    p.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ragged", "image2d", "precision"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "ragged", "image2d", "precision", "case"])
+    ap.add_argument("--case", default="1d", choices=["1d", "2d", "ragged"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--precision", default="fp32")
     ap.add_argument("--count", type=int, default=10000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -433,6 +469,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="1/16 of the batch (smoke runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="ragged: planner defaults instead of measured tiles")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -442,6 +479,8 @@ def main():
         run_image2d(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "case":
+        run_case(args)
     else:
         run_gpu(args)
 

@@ -59,6 +59,7 @@ struct GStage {
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
     int64_t pre_tab, post_tab;             // table offsets in the pool
     int64_t lo, hi;                        // four-step two-level table in the pool
+    int64_t line_tab;  // >= 0: the lines are separate transforms; line l starts at line_off[line_tab + l]
 };
 
 struct GTransform {
@@ -84,6 +85,7 @@ struct GExecArgs {
     int64_t spin_limit;
     int single;  // per-stage launch: item = item0 + blockIdx.x, no waits
     int item0;
+    const int64_t* line_off;  // element offsets of grouped lines (GStage::line_tab)
 };
 
 __device__ __forceinline__ int gpad(int a) { return a + (a >> 4); }
@@ -93,7 +95,7 @@ __device__ __forceinline__ int gpad(int a) { return a + (a >> 4); }
 template <int R, bool INV>
 __device__ __forceinline__ void g_pass(const GStage& st, const GShape& sh, int p, const float2* __restrict__ pool,
                                        const float2* src, float2* dst, int Lp, int line0, int nl, bool last,
-                                       float2* __restrict__ gout) {
+                                       float2* __restrict__ gout, const int64_t* __restrict__ line_off) {
     const int L = sh.L;
     const int Ns = sh.ns[p];
     const int stride = L / R;  // butterflies per line
@@ -127,7 +129,8 @@ __device__ __forceinline__ void g_pass(const GStage& st, const GShape& sh, int p
         } else {
             // natural order: output element k = b + r*stride of line line0+line
             const int aline = line0 + line;
-            const int64_t lo_line = (int64_t)aline * st.out_ls;
+            const int64_t lo_line =
+                st.line_tab >= 0 ? __ldg(line_off + st.line_tab + aline) : (int64_t)aline * st.out_ls;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int kk = b + r * stride;
@@ -152,30 +155,46 @@ __device__ __forceinline__ void g_pass(const GStage& st, const GShape& sh, int p
 template <bool INV>
 __device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __restrict__ pool,
                            const float2* __restrict__ gin, float2* __restrict__ gout, int line0, int nl,
-                           float2* smem) {
+                           float2* smem, const int64_t* __restrict__ line_off) {
     const int L = sh.L;
     const int Lp = gpad(L) + 1;
     float2* bufA = smem;
     float2* bufB = smem + kGBuf;
-    // 1. load (coalesced), pre-multiply, zero beyond in_valid
+    // 1. load (coalesced), pre-multiply, zero beyond in_valid; U loads in
+    // flight per thread before their shared-memory stores
     const int tot = nl * L;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        int line, i;
-        if (st.in_line_fast) {
-            line = e % nl;
-            i = e / nl;
-        } else {
-            line = e / L;
-            i = e - line * L;
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += U * kGThreads) {
+        float2 v[U];
+        int dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * kGThreads;
+            v[u] = make_float2(0.f, 0.f);
+            dst[u] = -1;
+            if (e < tot) {
+                int line, i;
+                if (st.in_line_fast) {
+                    line = e % nl;
+                    i = e / nl;
+                } else {
+                    line = e / L;
+                    i = e - line * L;
+                }
+                const int64_t lb = st.line_tab >= 0 ? __ldg(line_off + st.line_tab + line0 + line)
+                                                    : (int64_t)(line0 + line) * st.in_ls;
+                const int64_t off = lb + (int64_t)i * st.in_es;
+                dst[u] = line * Lp + gpad(i);
+                if (off < st.in_valid) {
+                    v[u] = __ldcg(gin + off);
+                    if (st.pre == G_PRE_TABLE) v[u] = cmul(v[u], __ldg(pool + st.pre_tab + off));
+                    else if (st.pre == G_PRE_TABLE_CONJ) v[u] = cmulc(v[u], __ldg(pool + st.pre_tab + off));
+                }
+            }
         }
-        const int64_t off = (int64_t)(line0 + line) * st.in_ls + (int64_t)i * st.in_es;
-        float2 v = make_float2(0.f, 0.f);
-        if (off < st.in_valid) {
-            v = __ldcg(gin + off);
-            if (st.pre == G_PRE_TABLE) v = cmul(v, __ldg(pool + st.pre_tab + off));
-            else if (st.pre == G_PRE_TABLE_CONJ) v = cmulc(v, __ldg(pool + st.pre_tab + off));
-        }
-        bufA[line * Lp + gpad(i)] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (dst[u] >= 0) bufA[dst[u]] = v[u];
     }
     __syncthreads();
     // 2./3. Stockham passes; the last one stores to global memory
@@ -186,7 +205,7 @@ __device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __r
         switch (sh.radix[p]) {
 #define B300_G(RR)                                                                    \
     case RR:                                                                          \
-        g_pass<RR, INV>(st, sh, p, pool, src, dst, Lp, line0, nl, last, gout);        \
+        g_pass<RR, INV>(st, sh, p, pool, src, dst, Lp, line0, nl, last, gout, line_off); \
         break;
             B300_G(1) B300_G(2) B300_G(3) B300_G(4) B300_G(5) B300_G(7) B300_G(8) B300_G(16)
 #undef B300_G
@@ -248,8 +267,8 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
     const int nl = min(st.lpt, st.nlines - line0);
     const float2* gin = g_buf_in(a, x, st.in_buf);
     float2* gout = g_buf_out(a, x, st.out_buf);
-    if (st.inv) g_tile_dir<true>(st, sh, a.pool, gin, gout, line0, nl, smem);
-    else g_tile_dir<false>(st, sh, a.pool, gin, gout, line0, nl, smem);
+    if (st.inv) g_tile_dir<true>(st, sh, a.pool, gin, gout, line0, nl, smem, a.line_off);
+    else g_tile_dir<false>(st, sh, a.pool, gin, gout, line0, nl, smem, a.line_off);
     if (s + 1 < x.nstages && !a.single) {
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "generic.cuh"
@@ -134,6 +136,7 @@ struct Builder {
 
 GStage base_stage(int shape, int nlines, int lpt, int inv) {
     GStage s{};
+    s.line_tab = -1;
     s.shape = shape;
     s.nlines = nlines;
     s.lpt = std::max(1, std::min(lpt, nlines));
@@ -177,7 +180,7 @@ bool split_four(int64_t n, int tile_max, int want_n2, int64_t* n1, int64_t* n2) 
 // Stages of one transform kind (length n); `lines` > 1 only for single-tile
 // uniform batches (every batch row is a line of one stage).
 bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int* nstages, int64_t* w1,
-                int64_t* w2) {
+                int64_t* w2, int64_t line_tab) {
     *w1 = *w2 = 0;
     std::vector<GStage> f, i;
     if (is_smooth(n) && n <= cfg.tile_max) {
@@ -190,6 +193,10 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
             s.in_ls = s.out_ls = n;
             s.in_es = s.out_es = 1;
             s.in_valid = s.out_valid = lines * n;
+            if (line_tab >= 0) {  // lines are separate transforms at line_off[line_tab + l]
+                s.line_tab = line_tab;
+                s.in_valid = s.out_valid = INT64_MAX;
+            }
             (d ? i : f).push_back(s);
         }
     } else if (is_smooth(n)) {
@@ -338,6 +345,7 @@ GExecArgs make_args(const GraphPlan* gp, const float2* in, float2* out, bool inv
     a.spin_limit = gp->spin_limit;
     a.single = single;
     a.item0 = item0;
+    a.line_off = gp->line_off;
     return a;
 }
 
@@ -349,7 +357,155 @@ bool graph_length_supported(int64_t n) {
     return next_pow2(2 * n - 1) <= (int64_t)kGTileMax * kGTileMax;
 }
 
+namespace {
+fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_t batch, bool ragged,
+                      const GLenConfig* force);
+}
+
 fft_status graph_plan_build(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_t batch, bool ragged) {
+    return build_impl(gp, lengths, batch, ragged, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, GLenConfig> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string device_name() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr{};
+    cudaGetDeviceProperties(&pr, dev);
+    std::string s = pr.name;
+    for (auto& c : s)
+        if (c == ' ') c = '_';
+    return s;
+}
+
+void tune_cache_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("FFT_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    GLenConfig c;
+    while (std::fscanf(f, "%255s %d %d %d %d", key, &c.tile_max, &c.split_n2, &c.lpt_a, &c.lpt_b) == 5)
+        g_tune_cache[key] = c;
+    std::fclose(f);
+}
+
+void tune_cache_store(const std::string& key, const GLenConfig& c, double us) {
+    g_tune_cache[key] = c;
+    const char* path = std::getenv("FFT_TUNE_CACHE");
+    if (!path) return;
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s %d %d %d %d %.2f\n", key.c_str(), c.tile_max, c.split_n2, c.lpt_a, c.lpt_b, us);
+        std::fclose(f);
+    }
+}
+
+std::vector<GLenConfig> tune_candidates(int64_t n, const GLenConfig& base) {
+    std::vector<GLenConfig> out;
+    auto halves = [](int cap) {
+        std::vector<int> v;
+        for (int l = cap; l >= 1 && (int)v.size() < 3; l /= 2) v.push_back(l);
+        return v;
+    };
+    if (is_smooth(n) && n <= base.tile_max) {
+        for (int l : halves(lines_per_tile((int)n, 0))) {
+            GLenConfig c = base;
+            c.lpt_a = l;
+            out.push_back(c);
+        }
+    } else if (is_smooth(n)) {
+        std::vector<std::pair<double, int64_t>> splits;
+        for (int64_t b = 2; b <= base.tile_max; ++b) {
+            if (n % b || n / b > base.tile_max || n / b < 2 || !is_smooth(b) || !is_smooth(n / b)) continue;
+            splits.push_back({std::fabs(std::log((double)(n / b)) - std::log((double)b)), b});
+        }
+        std::sort(splits.begin(), splits.end());
+        for (size_t si = 0; si < splits.size() && si < 3; ++si) {
+            const int64_t n2 = splits[si].second, n1 = n / n2;
+            for (int la : halves(lines_per_tile((int)n1, 0)))
+                for (int lb : halves(lines_per_tile((int)n2, 0))) {
+                    if (out.size() >= 24) break;
+                    GLenConfig c = base;
+                    c.split_n2 = (int)n2;
+                    c.lpt_a = la;
+                    c.lpt_b = lb;
+                    out.push_back(c);
+                }
+        }
+    }
+    if (out.empty()) out.push_back(base);
+    return out;
+}
+}  // namespace
+
+GLenConfig tune_length(int64_t n, int64_t count, const GLenConfig& base) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    const std::string key = device_name() + ":" + std::to_string(n);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+    std::vector<GLenConfig> cand = tune_candidates(n, base);
+    if (cand.size() == 1) return cand[0];
+    const int64_t reps = std::max<int64_t>(1, (int64_t(1) << 22) / n);
+    (void)count;
+    std::vector<int64_t> L((size_t)reps, n);
+    float2 *x = nullptr, *y = nullptr;
+    int* st = nullptr;
+    if (cudaMalloc(&x, sizeof(float2) * reps * n) != cudaSuccess || cudaMalloc(&y, sizeof(float2) * reps * n) != cudaSuccess ||
+        cudaMalloc(&st, sizeof(int)) != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(y);
+        return base;
+    }
+    cudaMemset(x, 0x3c, sizeof(float2) * reps * n);  // finite, non-zero values
+    cudaMemset(st, 0, sizeof(int));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    GLenConfig best = base;
+    float best_ms = 1e30f;
+    for (const GLenConfig& c : cand) {
+        GraphPlan tp;
+        tp.no_tune = true;
+        tp.use_graph = false;
+        if (build_impl(&tp, L, reps, true, &c) != FFT_OK) {
+            graph_plan_free(&tp);
+            continue;
+        }
+        graph_plan_exec(&tp, x, y, false, 0, st, false);
+        cudaEventRecord(e0);
+        for (int it2 = 0; it2 < 5; ++it2) graph_plan_exec(&tp, x, y, false, 0, st, false);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        graph_plan_free(&tp);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(st);
+    tune_cache_store(key, best, best_ms * 1e3 / 5);
+    return best;
+}
+
+namespace {
+fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_t batch, bool ragged,
+                      const GLenConfig* force) {
     Builder B;
     GLenConfig cfg;
     cfg.tile_max = env_i("B300FFT_G_TILE_MAX", kGTileMax);
@@ -367,18 +523,44 @@ fft_status graph_plan_build(GraphPlan* gp, const std::vector<int64_t>& lengths, 
         int first, nstages;
         int64_t w1, w2;
         int64_t lines;
+        bool group;  // ragged single-tile length: all its transforms are lines of one stage
     };
     std::map<int64_t, Kind> kinds;
-    const bool uniform = !ragged;
-    for (int64_t n : uniq) {
-        Kind k{};
-        k.first = (int)B.st_f.size();
-        const bool single_tile = is_smooth(n) && n <= cfg.tile_max;
-        k.lines = (uniform && single_tile) ? batch : 1;
-        if (k.lines > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
-        if (!build_kind(B, n, k.lines, cfg, &k.nstages, &k.w1, &k.w2)) return FFT_ERR_UNSUPPORTED;
-        kinds[n] = k;
+    std::map<int64_t, int64_t> count_of;
+    for (int64_t n : lengths) ++count_of[n];
+    // per-length tile configuration: planner defaults or measured (autotuner)
+    std::map<int64_t, GLenConfig> lcfg;
+    const bool tune = env_i("FFT_AUTOTUNE", 0) != 0 && !gp->no_tune;
+    for (int64_t n : uniq) lcfg[n] = force ? *force : (tune ? tune_length(n, ragged ? count_of[n] : batch, cfg) : cfg);
+    std::vector<int64_t> line_off;  // element offsets of grouped lines
+    {
+        // packed offset of every transform, for the grouped lengths
+        std::map<int64_t, std::vector<int64_t>> offs;
+        if (ragged) {
+            int64_t o = 0;
+            for (int64_t n : lengths) {
+                offs[n].push_back(o);
+                o += n;
+            }
+        }
+        const bool uniform = !ragged;
+        for (int64_t n : uniq) {
+            Kind k{};
+            k.first = (int)B.st_f.size();
+            const bool single_tile = is_smooth(n) && n <= lcfg[n].tile_max;
+            k.group = ragged && single_tile;
+            k.lines = single_tile ? (uniform ? batch : count_of[n]) : 1;
+            if (k.lines > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+            int64_t ltab = -1;
+            if (k.group) {
+                ltab = (int64_t)line_off.size();
+                line_off.insert(line_off.end(), offs[n].begin(), offs[n].end());
+            }
+            if (!build_kind(B, n, k.lines, lcfg[n], &k.nstages, &k.w1, &k.w2, ltab)) return FFT_ERR_UNSUPPORTED;
+            kinds[n] = k;
+        }
     }
+    gp->configs = lcfg;
 
     // transforms (packed offsets), workspace, counters
     std::vector<GTransform> xf;
@@ -399,8 +581,10 @@ fft_status graph_plan_build(GraphPlan* gp, const std::vector<int64_t>& lengths, 
         xf.push_back(x);
     };
     if (ragged) {
+        for (auto& kv : kinds)
+            if (kv.second.group) add_xf(kv.first, 0);  // one transform holds every line of the length
         for (int64_t n : lengths) {
-            add_xf(n, off);
+            if (!kinds[n].group) add_xf(n, off);
             off += n;
         }
     } else {
@@ -465,6 +649,7 @@ fft_status graph_plan_build(GraphPlan* gp, const std::vector<int64_t>& lengths, 
     if (upload(&gp->stages[1], B.st_i) != cudaSuccess) return FFT_ERR_ALLOC;
     if (upload(&gp->xf, xf) != cudaSuccess) return FFT_ERR_ALLOC;
     if (upload(&gp->items, items) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (upload(&gp->line_off, line_off) != cudaSuccess) return FFT_ERR_ALLOC;
     gp->nitems = (int)items.size();
     gp->ncounters = ctr;
     gp->ntransforms = (int)xf.size();
@@ -489,8 +674,11 @@ fft_status graph_plan_build(GraphPlan* gp, const std::vector<int64_t>& lengths, 
     if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
 }
+}  // namespace
 
 void graph_plan_free(GraphPlan* gp) {
+    cudaFree(gp->line_off);
+    gp->line_off = nullptr;
     for (int d = 0; d < 2; ++d) {
         if (gp->gexec[d]) cudaGraphExecDestroy(gp->gexec[d]);
         if (gp->graph[d]) cudaGraphDestroy(gp->graph[d]);

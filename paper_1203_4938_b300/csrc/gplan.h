@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -44,7 +45,15 @@ struct GraphPlan {
     bool use_graph = true;
     int64_t spin_limit = int64_t(1) << 23;
     std::string desc;
+    int64_t* line_off = nullptr;              // grouped-line offsets (device)
+    bool no_tune = false;                     // candidate plans built by the autotuner
+    std::map<int64_t, GLenConfig> configs;    // tile configuration used per length
 };
+
+// Measured tile configuration of one length (the autotuner): candidates are
+// timed as ragged plans of ~2^22 elements of that length; results are cached
+// per process and, when FFT_TUNE_CACHE names a file, in that file.
+GLenConfig tune_length(int64_t n, int64_t count, const GLenConfig& base);
 
 // Build a plan for transforms of the given lengths, packed back to back
 // (offsets = exclusive prefix sum), or for `batch` copies of one length when

@@ -55,6 +55,13 @@ struct P2Plan {
 
 __host__ __device__ __forceinline__ constexpr int padi(int a) { return a + (a >> 4); }
 
+// Radix-16 passes read 6 of their 15 twiddles and form the rest by one
+// complex product (fewer load/store-unit instructions, more FMA work).
+#ifndef B300_TW_LOADS6
+#define B300_TW_LOADS6 1
+#endif
+constexpr bool kTwiddleLoads6 = B300_TW_LOADS6 != 0;
+
 // Streaming (evict-first) global accesses for the data; tables use __ldg.
 __device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
 __device__ __forceinline__ void st_stream(float2* p, float2 v) { __stcs(p, v); }
@@ -102,7 +109,24 @@ __device__ __forceinline__ void dft_at(float2* v) {
 template <class PL, int P, bool INV>
 __device__ __forceinline__ void pass_compute(float2 (&v)[PL::R], int b0, const float2* __restrict__ tw) {
     constexpr int Rp = PL::radix(P), Q = PL::R / Rp, Ns = PL::ns(P);
-    if constexpr (P > 0) {
+    if constexpr (P > 0 && Rp == 16 && Q == 1 && kTwiddleLoads6) {
+        // six table loads (W^k, W^2k, W^3k, W^4k, W^8k, W^12k); the other nine
+        // twiddles are one complex product of two table values each
+        const float2* tp = tw + PL::twoff(P) + (b0 & (Ns - 1));
+        float2 w[16];
+        w[1] = __ldg(tp);
+        w[2] = __ldg(tp + Ns);
+        w[3] = __ldg(tp + 2 * Ns);
+        w[4] = __ldg(tp + 3 * Ns);
+        w[8] = __ldg(tp + 7 * Ns);
+        w[12] = __ldg(tp + 11 * Ns);
+#pragma unroll
+        for (int h = 4; h <= 12; h += 4)
+#pragma unroll
+            for (int l = 1; l <= 3; ++l) w[h + l] = cmul(w[h], w[l]);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], w[r]);
+    } else if constexpr (P > 0) {
         const float2* twp = tw + PL::twoff(P);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -118,29 +142,47 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[PL::R], int b0, const f
     for (int q = 0; q < Q; ++q) dft_at<Rp, Q, INV>(v + q);
 }
 
-// Scatter the outputs of pass P into the exchange buffer (padded indices).
-template <class PL, int P>
-__device__ __forceinline__ void pass_scatter(const float2 (&v)[PL::R], int b0, float2* s, int cstride, int coff) {
-    constexpr int Rp = PL::radix(P), Q = PL::R / Rp, Ns = PL::ns(P), L = Ns * Rp;
+// Shared-memory addresses: element a of column c (column stride CS, the
+// number of interleaved columns) lives at padi(a*CS + c).  Since
+// padi(x + 16m) = padi(x) + 17m, every address below is a per-thread base plus
+// a compile-time offset, so each access is one shared load/store with an
+// immediate offset.
+
+// Scatter the outputs of pass P into the exchange buffer.
+template <class PL, int P, int CS>
+__device__ __forceinline__ void pass_scatter(const float2 (&v)[PL::R], int b0, float2* s, int coff) {
+    constexpr int Rp = PL::radix(P), Q = PL::R / Rp, Ns = PL::ns(P);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int b = b0 + q * PL::T;
         const int k = b & (Ns - 1);
         const int base = (b - k) * Rp + k;
+        if constexpr ((Ns * CS) % 16 == 0) {
+            float2* p = s + padi(base * CS + coff);
 #pragma unroll
-        for (int r = 0; r < Rp; ++r) {
-            const int a = (base + r * Ns) * cstride + coff;
-            s[padi(a)] = v[q + Q * r];
+            for (int r = 0; r < Rp; ++r) p[r * (Ns * CS / 16) * 17] = v[q + Q * r];
+        } else if constexpr (Ns == 1 && Rp == 16 && 16 % CS == 0) {
+            float2* p = s + 17 * b * CS + coff;  // base = 16 b, coff < CS
+#pragma unroll
+            for (int r = 0; r < Rp; ++r) p[r * CS + ((r * CS) >> 4)] = v[q + Q * r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < Rp; ++r) s[padi((base + r * Ns) * CS + coff)] = v[q + Q * r];
         }
     }
-    (void)L;
 }
 
 // Gather the pass inputs x[t + i*T] from the exchange buffer.
-template <class PL>
-__device__ __forceinline__ void pass_gather(float2 (&v)[PL::R], int t, const float2* s, int cstride, int coff) {
+template <class PL, int CS>
+__device__ __forceinline__ void pass_gather(float2 (&v)[PL::R], int t, const float2* s, int coff) {
+    if constexpr ((PL::T * CS) % 16 == 0) {
+        const float2* p = s + padi(t * CS + coff);
 #pragma unroll
-    for (int i = 0; i < PL::R; ++i) v[i] = s[padi((t + i * PL::T) * cstride + coff)];
+        for (int i = 0; i < PL::R; ++i) v[i] = p[i * (PL::T * CS / 16) * 17];
+    } else {
+#pragma unroll
+        for (int i = 0; i < PL::R; ++i) v[i] = s[padi((t + i * PL::T) * CS + coff)];
+    }
 }
 
 // Barrier over the threads that share an exchange buffer.
@@ -150,18 +192,17 @@ __device__ __forceinline__ void xsync() {
     else __syncthreads();
 }
 
-// All passes from P on.  Data layout in the exchange buffer: element a of
-// column c at index a*cstride + coff (rows kernel: cstride 1, coff 0).
-template <class PL, int P, bool INV, bool WARP_ONLY>
-__device__ __forceinline__ void run_passes(float2 (&v)[PL::R], int t, float2* s, int cstride, int coff,
+// All passes from P on (CS interleaved columns in the exchange buffer).
+template <class PL, int P, bool INV, bool WARP_ONLY, int CS>
+__device__ __forceinline__ void run_passes(float2 (&v)[PL::R], int t, float2* s, int coff,
                                            const float2* __restrict__ tw) {
     pass_compute<PL, P, INV>(v, t, tw);
     if constexpr (P + 1 < PL::NPASS) {
-        pass_scatter<PL, P>(v, t, s, cstride, coff);
+        pass_scatter<PL, P, CS>(v, t, s, coff);
         xsync<WARP_ONLY>();
-        pass_gather<PL>(v, t, s, cstride, coff);
+        pass_gather<PL, CS>(v, t, s, coff);
         xsync<WARP_ONLY>();
-        run_passes<PL, P + 1, INV, WARP_ONLY>(v, t, s, cstride, coff, tw);
+        run_passes<PL, P + 1, INV, WARP_ONLY, CS>(v, t, s, coff, tw);
     }
 }
 
@@ -172,10 +213,10 @@ template <class PL, int P, bool INV>
 __device__ __forceinline__ void run_passes_to_last(float2 (&v)[PL::R], int t, float2* s,
                                                    const float2* __restrict__ tw) {
     pass_compute<PL, P, INV>(v, t, tw);
-    pass_scatter<PL, P>(v, t, s, 1, 0);
+    pass_scatter<PL, P, 1>(v, t, s, 0);
     __syncthreads();
     if constexpr (P + 2 < PL::NPASS) {
-        pass_gather<PL>(v, t, s, 1, 0);
+        pass_gather<PL, 1>(v, t, s, 0);
         __syncthreads();
         run_passes_to_last<PL, P + 1, INV>(v, t, s, tw);
     }
@@ -208,7 +249,7 @@ __device__ __forceinline__ void rows_tile(const float2* __restrict__ src, float2
     float2 v[PL::R];
 #pragma unroll
     for (int i = 0; i < PL::R; ++i) v[i] = ok ? ldx<LK>(src + t + i * PL::T) : make_float2(0.f, 0.f);
-    run_passes<PL, 0, INV, false>(v, t, smem + sub * PL::PADDED, 1, 0, tw);
+    run_passes<PL, 0, INV, false, 1>(v, t, smem + sub * PL::PADDED, 0, tw);
     if (ok) {
 #pragma unroll
         for (int i = 0; i < PL::R; ++i) stx<SK>(dst + t + i * PL::T, v[i], pol);
@@ -247,8 +288,14 @@ __device__ __forceinline__ void rowsT_tile(const float2* __restrict__ src, float
     const int c = threadIdx.x % TPC;
     const int t2 = threadIdx.x / TPC;
     const float2* sc = smem + c * CF::PITCH;
+    if constexpr (PL::T % 16 == 0) {
+        const float2* p = sc + padi(t2);
 #pragma unroll
-    for (int i = 0; i < PL::R; ++i) v[i] = sc[padi(t2 + i * PL::T)];
+        for (int i = 0; i < PL::R; ++i) v[i] = p[i * (PL::T / 16) * 17];
+    } else {
+#pragma unroll
+        for (int i = 0; i < PL::R; ++i) v[i] = sc[padi(t2 + i * PL::T)];
+    }
     pass_compute<PL, PL::NPASS - 1, INV>(v, t2, tw);
     float2* d0 = dst + c;
 #pragma unroll
@@ -301,7 +348,7 @@ __device__ __forceinline__ void cols_tile(const float2* __restrict__ src, float2
         if constexpr (PL::NPASS == 1) __syncthreads();
     }
 
-    run_passes<PL, 0, INV, false>(v, t, smem, C, c, tw);
+    run_passes<PL, 0, INV, false, C>(v, t, smem, c, tw);
 
     if constexpr (TW) {
         const float2 w0 = root2(tw_lo, tw_hi, (col0 + (uint32_t)c) * (uint32_t)t, sh);

@@ -230,8 +230,8 @@ __device__ __forceinline__ void tc_dft16(float2 (&v)[16], TcCtx& c, int ntiles) 
 
 // Stockham passes of a 16^k transform with tensor-core butterflies.  Same
 // thread layout and exchange as run_passes (R = 16, one butterfly per thread).
-template <class PL, int P, bool INV, int MODE>
-__device__ __forceinline__ void tc_run_passes(float2 (&v)[16], int t, float2* s, int cstride, int coff,
+template <class PL, int P, bool INV, int MODE, int CS>
+__device__ __forceinline__ void tc_run_passes(float2 (&v)[16], int t, float2* s, int coff,
                                               const float2* __restrict__ tw, TcCtx& c, int ntiles) {
     static_assert(PL::R == 16 && PL::radix(P) == 16, "tensor-core passes are radix 16");
     constexpr int Ns = PL::ns(P);
@@ -243,11 +243,11 @@ __device__ __forceinline__ void tc_run_passes(float2 (&v)[16], int t, float2* s,
     }
     tc_dft16<MODE>(v, c, ntiles);
     if constexpr (P + 1 < PL::NPASS) {
-        pass_scatter<PL, P>(v, t, s, cstride, coff);
+        pass_scatter<PL, P, CS>(v, t, s, coff);
         __syncthreads();
-        pass_gather<PL>(v, t, s, cstride, coff);
+        pass_gather<PL, CS>(v, t, s, coff);
         __syncthreads();
-        tc_run_passes<PL, P + 1, INV, MODE>(v, t, s, cstride, coff, tw, c, ntiles);
+        tc_run_passes<PL, P + 1, INV, MODE, CS>(v, t, s, coff, tw, c, ntiles);
     }
 }
 
@@ -329,7 +329,7 @@ k_tc_rows(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows
     float2 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = ok ? ld_stream(src + t + i * PL::T) : make_float2(0.f, 0.f);
-    tc_run_passes<PL, 0, INV, MODE>(v, t, xs + sub * PL::PADDED, 1, 0, tw, c, CF::THREADS / 128);
+    tc_run_passes<PL, 0, INV, MODE, 1>(v, t, xs + sub * PL::PADDED, 0, tw, c, CF::THREADS / 128);
     if (ok) {
         float2* dst = out + row * PL::N;
 #pragma unroll
@@ -365,7 +365,7 @@ k_tc_cols256(const float2* __restrict__ in, float2* __restrict__ out, int64_t S,
         const int c2 = j % C, ii = j / C;
         steps[ii * C + c2] = root2(lo, hi, (uint32_t)(g * C + c2) * (uint32_t)(ii * PL::T), sh);
     }
-    tc_run_passes<PL, 0, INV, MODE>(v, t, xs, C, cc, tw, c, 2);
+    tc_run_passes<PL, 0, INV, MODE, C>(v, t, xs, cc, tw, c, 2);
     const float2 w0 = root2(lo, hi, (uint32_t)col * (uint32_t)t, sh);
     float2* dst = out + item * item_stride + col;
 #pragma unroll
@@ -400,7 +400,7 @@ k_tc_rowsT256(const float2* __restrict__ in, float2* __restrict__ out, const flo
     // pass 0 (row-major mapping), exchange
     tc_dft16<MODE>(v, c, 2);
     float2* sx = xs + sub * CF::PITCH;
-    pass_scatter<PL, 0>(v, t, sx, 1, 0);
+    pass_scatter<PL, 0, 1>(v, t, sx, 0);
     __syncthreads();
     // pass 1 re-mapped: row r = threadIdx % 16, butterfly t2 = threadIdx / 16
     const int r = threadIdx.x % TPC, t2 = threadIdx.x / TPC;

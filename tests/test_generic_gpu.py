@@ -128,3 +128,17 @@ def test_ragged_graph_capture_by_caller(torch):
         g.replay()
         torch.cuda.synchronize()
         assert max_rel_l2(out2.cpu().numpy()[None], ref[None], -1) <= TOL_FP32
+
+
+def test_ragged_autotuned_tiles_and_cache(torch, monkeypatch, tmp_path):
+    """FFT_AUTOTUNE=1 times candidate tile shapes per length; the choice is
+    written to FFT_TUNE_CACHE and the plan is still exact to 1e-6."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("FFT_AUTOTUNE", "1")
+    monkeypatch.setenv("FFT_TUNE_CACHE", str(cache))
+    lengths = [96, 640, 4096, 7 * 2 ** 11, 3 * 2 ** 13, 65536, 1024, 96, 101]
+    data = np.random.default_rng(8).uniform(-1, 1, 2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    for per_size in (False, True):
+        assert _ragged_check(torch, lengths, data, per_size, -1) <= TOL_FP32
+    text = cache.read_text().split()
+    assert len(text) >= 6 and any(t.endswith(":65536") for t in text)
