@@ -45,6 +45,21 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Slowest rank's time (the job finishes when the last replica does)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(flops_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job GFLOP/s: every rank runs the full workload (replicas, weak
+    scaling) and the job takes as long as the slowest rank."""
+    return world * flops_per_rank / (ms_max * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -214,9 +229,7 @@ def run_gpu(args):
     clocks = clk.stop()
     ms = t0.elapsed_time(t1) / args.steps
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(ms, dev)
 
     # per-kernel durations inside the timed region
     per = {}
@@ -240,7 +253,7 @@ def run_gpu(args):
     share = tot[dom] / sum(tot.values())
 
     fl = sum(2 * 5.0 * n * b * k for k, n, b in sizes)
-    value = world * fl / (ms * 1e-3) / 1e9
+    value = job_throughput(fl, world, ms)
 
     # end to end through the public API: pinned host input -> device, fwd+inv, result -> host
     e2e = None

@@ -95,11 +95,11 @@ int env_int(const char* name, int dflt) {
 // Persistent four-step: both passes in one launch with L2-resident chunks.
 fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
     // Measured best (l1, c, l2, tpc, chunk MiB) per log2 N on a B300 with 2^26
-    // elements per exec; 2^15 is faster as two launches, so it has no entry.
+    // elements per exec (2^13 and 2^14 are faster as one single-CTA pass).
     static const int kCfg[25][5] = {
-        {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
-        {8, 16, 8, 16, 16}, {8, 16, 9, 8, 16}, {8, 16, 10, 4, 16}, {9, 16, 10, 8, 16}, {10, 8, 10, 8, 16},
-        {11, 4, 10, 8, 16}, {11, 4, 11, 4, 48}, {12, 4, 11, 8, 16}, {12, 4, 12, 4, 48}};
+        {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
+        {7, 32, 8, 16, 32}, {8, 16, 8, 16, 16}, {8, 16, 9, 8, 32}, {8, 16, 10, 4, 32}, {9, 16, 10, 8, 16},
+        {10, 8, 10, 8, 16}, {11, 4, 10, 8, 16}, {11, 4, 11, 4, 32}, {12, 4, 11, 8, 48}, {12, 4, 12, 4, 8}};
     const bool forced = std::getenv("B300FFT_PERSIST_CFG") != nullptr;
     if (logn > 24 || (kCfg[logn][0] == 0 && !forced)) return FFT_ERR_UNSUPPORTED;
     PersistConfig cfg{kCfg[logn][0], kCfg[logn][1], kCfg[logn][2], kCfg[logn][3]};

@@ -7,6 +7,7 @@
 namespace b300fft {
 
 #define B300_PERSIST_CONFIGS(X)                                                                             \
+    X(6, 32, 7, 16) X(7, 16, 7, 16) X(7, 32, 7, 32) X(7, 32, 8, 16)                                           \
     X(7, 16, 8, 8) X(8, 16, 8, 16) X(8, 8, 8, 8) X(8, 16, 9, 8) X(9, 8, 9, 8) X(8, 16, 10, 4) X(9, 8, 10, 4) \
         X(9, 16, 10, 8) X(10, 4, 10, 4) X(10, 8, 10, 8) X(10, 4, 11, 2) X(11, 4, 10, 8) X(11, 4, 11, 4)     \
             X(11, 2, 11, 2) X(11, 4, 12, 2) X(12, 4, 11, 8) X(12, 4, 12, 4) X(12, 2, 12, 2)
