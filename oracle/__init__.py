@@ -83,6 +83,8 @@ class OracleLib:
                                          ctypes.c_int]
         lib.oracle_fft2d.argtypes = [dp, dp, i64, i64, i64, ctypes.c_int,
                                      ctypes.c_int]
+        lib.oracle_circ_conv.argtypes = [dp, dp, dp, i64, ctypes.c_int]
+        lib.oracle_circ_conv.restype = ctypes.c_int
         lib.oracle_num_cpus.argtypes = []
         for f in ("oracle_dft_naive", "oracle_dft_bins", "oracle_fft_radix2",
                   "oracle_fft_split_m", "oracle_fft", "oracle_fft_batch",
@@ -137,6 +139,20 @@ class OracleLib:
                                          threads), "fft_batch")
         return y
 
+    def circ_conv(self, x, h, corr: bool = False) -> np.ndarray:
+        """Circular convolution (or correlation) of each row of x with h, by
+        the definition, O(N^2) per row."""
+        x = _c128(x)
+        h = _c128(h).reshape(-1)
+        n = x.shape[-1]
+        assert h.shape[0] == n
+        flat = x.reshape(-1, n)
+        y = np.empty_like(flat)
+        for b in range(flat.shape[0]):
+            _check(self.lib.oracle_circ_conv(_ptr(flat[b]), _ptr(h), _ptr(y[b]), n, int(bool(corr))),
+                   "circ_conv")
+        return y.reshape(x.shape)
+
     def fft2(self, x, sign: int = FORWARD, threads: int = 0) -> np.ndarray:
         """2-D DFT over the last two axes: rows first, then columns."""
         x = _c128(x)
@@ -184,6 +200,10 @@ def fft(x, sign: int = FORWARD, threads: int = 0) -> np.ndarray:
 
 def fft2(x, sign: int = FORWARD, threads: int = 0) -> np.ndarray:
     return default().fft2(x, sign, threads)
+
+
+def circ_conv(x, h, corr: bool = False) -> np.ndarray:
+    return default().circ_conv(x, h, corr)
 
 
 def rel_l2(y, ref) -> np.ndarray:

@@ -287,3 +287,34 @@ int oracle_fft2d(const double *x, double *y, int64_t h, int64_t w, int64_t batch
     free(fc);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Circular convolution and correlation by their definitions (the paper's   */
+/* Sec. III-A names convolution among the uses of the DFT):                  */
+/*   corr = 0:  y[m] = sum_j x[j] h[(m - j) mod N]                           */
+/*   corr = 1:  y[m] = sum_j x[(j + m) mod N] conj(h[j])                     */
+/* ------------------------------------------------------------------------ */
+int oracle_circ_conv(const double *x, const double *h, double *y, int64_t n, int corr)
+{
+    if (n <= 0) return -1;
+    for (int64_t m = 0; m < n; ++m) {
+        double sr = 0.0, si = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double xr, xi, hr, hi;
+            if (!corr) {
+                int64_t q = ((m - j) % n + n) % n;
+                xr = x[2 * j]; xi = x[2 * j + 1];
+                hr = h[2 * q]; hi = h[2 * q + 1];
+            } else {
+                int64_t q = (j + m) % n;
+                xr = x[2 * q]; xi = x[2 * q + 1];
+                hr = h[2 * j]; hi = -h[2 * j + 1];
+            }
+            sr += xr * hr - xi * hi;
+            si += xr * hi + xi * hr;
+        }
+        y[2 * m] = sr;
+        y[2 * m + 1] = si;
+    }
+    return 0;
+}

@@ -251,10 +251,41 @@ def pin_image_dc_and_spikes(o):
     _close(X[-fy % h, -fx % w] - Xi[-fy % h, -fx % w], 1j * spike, 1e-9, "spike -")
 
 
+def pin_convolution(o):
+    """Circular convolution / correlation: impulse kernel is the identity, a
+    shifted impulse shifts (conv) or shifts back (corr), a constant kernel
+    sums, hand-evaluated 4-point case, commutativity, and the convolution
+    theorem against the torch.fft witness."""
+    import torch
+    for i, n in enumerate([1, 2, 3, 7, 16, 30, 97]):
+        x = _rand(n, 1300 + i)
+        d = np.zeros(n, complex)
+        d[0] = 1
+        _close(o.circ_conv(x, d), x, 1e-13, f"conv identity n={n}")
+        _close(o.circ_conv(x, d, corr=True), x, 1e-13, f"corr identity n={n}")
+        s = (3 * n) // 5
+        ds = np.zeros(n, complex)
+        ds[s] = 1
+        _close(o.circ_conv(x, ds), np.roll(x, s), 1e-13, f"conv shift n={n}")
+        _close(o.circ_conv(x, ds, corr=True), np.roll(x, -s), 1e-13, f"corr shift n={n}")
+        c = np.full(n, 0.5 - 0.25j)
+        _close(o.circ_conv(x, c), np.full(n, (0.5 - 0.25j) * x.sum()), 1e-12, f"conv constant n={n}")
+        h = _rand(n, 1400 + i)
+        _close(o.circ_conv(x, h), o.circ_conv(h, x), 1e-12, f"conv commutes n={n}")
+        tx, th = torch.from_numpy(x), torch.from_numpy(h)
+        conv = torch.fft.ifft(torch.fft.fft(tx) * torch.fft.fft(th)).numpy()
+        corr = torch.fft.ifft(torch.fft.fft(tx) * torch.fft.fft(th).conj()).numpy()
+        _close(o.circ_conv(x, h), conv, 1e-11, f"conv theorem n={n}")
+        _close(o.circ_conv(x, h, corr=True), corr, 1e-11, f"corr theorem n={n}")
+    # [1,2,3,4] (*) [1,1,0,0]: y[m] = x[m] + x[m-1] = [5, 3, 5, 7]
+    _close(o.circ_conv(np.array([1, 2, 3, 4], complex), np.array([1, 1, 0, 0], complex)),
+           np.array([5, 3, 5, 7], complex), 1e-14, "conv 4-point")
+
+
 ALL_PINS = [pin_golden, pin_impulse, pin_shifted_impulse, pin_constant, pin_tone,
             pin_parseval, pin_linearity, pin_shift, pin_conjugate_symmetry,
             pin_round_trip, pin_brute_force, pin_batch, pin_library_witness,
-            pin_2d, pin_image_dc_and_spikes]
+            pin_2d, pin_image_dc_and_spikes, pin_convolution]
 
 
 def failing_pins(o):

@@ -37,6 +37,8 @@ MUTANTS = [
     ("bins_off_by_one", "int64_t k = ks[t] % n;", "int64_t k = (ks[t] + 1) % n;"),
     ("2d_column_reversed", "img[2 * (r * w + c)] = fc[2 * (c * h + r)];",
      "img[2 * (r * w + c)] = fc[2 * (c * h + (h - 1 - r))];"),
+    ("conv_index_sign", "int64_t q = ((m - j) % n + n) % n;", "int64_t q = ((m + j) % n + n) % n;"),
+    ("corr_missing_conj", "hr = h[2 * j]; hi = -h[2 * j + 1];", "hr = h[2 * j]; hi = h[2 * j + 1];"),
     ("2d_rows_only", "rc = oracle_fft_batch(col, fc, h, w, sign, nthreads);",
      "memcpy(fc, col, sizeof(double) * 2 * (size_t)(h * w)); rc = 0;"),
 ]
