@@ -95,6 +95,28 @@ FFT_API fft_plan fft_plan_create(int dims, const int64_t *lengths, int64_t batch
  * once into a CUDA graph at plan time.  precision must be FFT_FP32. */
 FFT_API fft_plan fft_plan_create_ragged(const int64_t *lengths, int64_t count, int precision);
 
+/* Create a plan for `batch` real transforms of even length n (half spectrum).
+ * fft_exec with FFT_FORWARD maps real input [batch][n] (floats) to complex
+ * output [batch][n/2+1] (bins 0..n/2 of the DFT of the paper's Sec. III-A;
+ * the rest follow from X[n-k] = conj(X[k])); FFT_INVERSE maps [batch][n/2+1]
+ * complex (a Hermitian half spectrum) to [batch][n] real, unnormalised, so
+ * inverse(forward(x)) = n x.  Built on the complex plan of length n/2 (any
+ * length fft_plan_create supports) plus one split pass; the plan holds an
+ * n/2 * batch complex workspace.  NULL on error (odd n: FFT_ERR_UNSUPPORTED). */
+FFT_API fft_plan fft_plan_create_real(int64_t n, int64_t batch);
+
+/* Spectrum product of FFT convolution / correlation (the paper's Sec. III-A
+ * names convolution among the DFT's uses):
+ *     out[t][k] = scale * a[t][k] * b[k]          (conj_b = 0: convolution)
+ *     out[t][k] = scale * a[t][k] * conj(b[k])    (conj_b != 0: correlation)
+ * for t < batch, k < n; a, out: [batch][n] complex64 (out == a allowed),
+ * b: [n] complex64 broadcast over the batch; device pointers, 16-byte
+ * aligned.  With a = DFT(x), b = DFT(h) and scale = 1/n, the inverse
+ * transform of out is the circular convolution (correlation) of x with h.
+ * Asynchronous on `stream`. */
+FFT_API fft_status fft_spectrum_product(const void *a, const void *b, void *out, int64_t n, int64_t batch,
+                                        float scale, int conj_b, void *stream);
+
 /* Status of the last fft_plan_create* call on this host thread. */
 FFT_API fft_status fft_last_error(void);
 

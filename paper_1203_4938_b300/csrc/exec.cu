@@ -57,6 +57,9 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                                 nullptr, nullptr, 0, st);
             break;
         }
+        case PlanKind::Real:
+            if (!want(0)) return FFT_OK;
+            return exec_real(p, in, out, inv, st);
         case PlanKind::TensorCore:
             return exec_tc(p, in, out, inv, st, only);
         case PlanKind::Generic:

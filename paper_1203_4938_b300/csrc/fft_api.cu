@@ -67,6 +67,10 @@ void destroy_plan_resources(fft_plan_s* p) {
     p->d_work = nullptr;
     p->d_status = nullptr;
     p->d_aux = nullptr;
+    if (p->inner) {
+        fft_plan_destroy(p->inner);
+        p->inner = nullptr;
+    }
     if (p->gplan) {
         graph_plan_free(p->gplan);
         delete p->gplan;
@@ -330,6 +334,24 @@ fft_plan fft_plan_create(int dims, const int64_t* lengths, int64_t batch, int pr
         if (lh >= 0 && lw >= 0) s = build_pow2_2d(p, lh, lw);
         else s = FFT_ERR_UNSUPPORTED;
     }
+    if (s != FFT_OK) return fail(s, p);
+    return finish(p);
+}
+
+fft_plan fft_plan_create_real(int64_t n, int64_t batch) {
+    g_last_error = FFT_OK;
+    if (n < 2 || batch < 1 || n > (int64_t(1) << 31) || batch > (int64_t(1) << 40) / n)
+        return fail(FFT_ERR_INVALID_ARG, nullptr);
+    if (n & 1) return fail(FFT_ERR_UNSUPPORTED, nullptr);
+    fft_plan_s* p = new (std::nothrow) fft_plan_s();
+    if (!p) return fail(FFT_ERR_ALLOC, nullptr);
+    p->dims = 1;
+    p->len[0] = n;
+    p->batch = batch;
+    p->elements = n * batch;
+    if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_ALLOC, p);
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return fail(FFT_ERR_CUDA, p);
+    fft_status s = build_real_plan(p, n, batch);
     if (s != FFT_OK) return fail(s, p);
     return finish(p);
 }

@@ -18,7 +18,8 @@ enum class PlanKind : int {
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
     Ragged,    // persistent work-queue kernel over uneven lengths
-    TensorCore // radix-16 stages as tensor-core GEMMs
+    TensorCore, // radix-16 stages as tensor-core GEMMs
+    Real        // real-to-complex / complex-to-real around a complex plan of N/2
 };
 
 struct GraphPlan;  // gplan.h
@@ -59,6 +60,7 @@ struct fft_plan_s {
     cudaGraphExec_t graph_exec = nullptr;
 
     b300fft::GraphPlan* gplan = nullptr;  // Generic / Ragged kinds
+    fft_plan inner = nullptr;             // Real kind: the complex plan of N/2
     b300fft::TcPlan* tc = nullptr;
 
     int kernels = 0;
@@ -78,5 +80,7 @@ fft_status build_generic_1d(fft_plan_s* p);
 fft_status build_ragged(fft_plan_s* p, const int64_t* lengths, int64_t count);
 fft_status build_tc_plan(fft_plan_s* p);
 fft_status exec_tc(fft_plan_s* p, const float2* in, float2* out, bool inv, cudaStream_t st, int only);
+fft_status build_real_plan(fft_plan_s* p, int64_t n, int64_t batch);
+fft_status exec_real(fft_plan_s* p, const void* in, void* out, bool inv, cudaStream_t st);
 
 }  // namespace b300fft

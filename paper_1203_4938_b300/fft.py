@@ -42,7 +42,7 @@ PRECISIONS = {"fp32": FFT_FP32, "tc_fp16": FFT_TC_FP16, "tc_bf16": FFT_TC_BF16,
 EXPORTS = ("fft_plan_create", "fft_plan_create_ragged", "fft_last_error", "fft_exec",
            "fft_plan_check", "fft_plan_destroy", "fft_plan_workspace_bytes", "fft_status_string",
            "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size",
-           "fft_exec_pow2_static")
+           "fft_exec_pow2_static", "fft_plan_create_real", "fft_spectrum_product")
 
 _lock = threading.Lock()
 _lib = None
@@ -70,6 +70,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fft_plan_create.restype = vp
         lib.fft_plan_create_ragged.argtypes = [i64p, ctypes.c_int64, ctypes.c_int]
         lib.fft_plan_create_ragged.restype = vp
+        lib.fft_spectrum_product.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                                             ctypes.c_int, vp]
+        lib.fft_spectrum_product.restype = ctypes.c_int
+        lib.fft_plan_create_real.argtypes = [ctypes.c_int64, ctypes.c_int64]
+        lib.fft_plan_create_real.restype = vp
         lib.fft_last_error.argtypes = []
         lib.fft_last_error.restype = ctypes.c_int
         lib.fft_exec.argtypes = [vp, vp, vp, ctypes.c_int, vp]
@@ -113,6 +118,17 @@ def fft_plan_create(dims: int, lengths, batch: int, precision: int = FFT_FP32):
 def fft_plan_create_ragged(lengths, count: int, precision: int = FFT_FP32):
     h = load().fft_plan_create_ragged(_i64_array(lengths), int(count), int(precision))
     return h or None
+
+
+def fft_plan_create_real(n: int, batch: int):
+    h = load().fft_plan_create_real(int(n), int(batch))
+    return h or None
+
+
+def fft_spectrum_product(a_ptr: int, b_ptr: int, out_ptr: int, n: int, batch: int, scale: float,
+                         conj_b: bool = False, stream: int = 0) -> int:
+    return int(load().fft_spectrum_product(a_ptr, b_ptr, out_ptr, int(n), int(batch), float(scale),
+                                           int(bool(conj_b)), stream or None))
 
 
 def fft_last_error() -> int:
@@ -288,3 +304,65 @@ class Ragged(Plan):
     @property
     def shape(self):
         return (self.numel,)
+
+
+class RealPlan(Plan):
+    """Real <-> half-spectrum plan: forward() takes float32 [batch, n] and
+    returns complex64 [batch, n/2+1]; inverse() the reverse (unnormalised)."""
+
+    def __init__(self, n: int, batch: int = 1):
+        self.lengths = (int(n),)
+        self.batch = int(batch)
+        self.precision = FFT_FP32
+        self.handle = fft_plan_create_real(n, batch)
+        if self.handle is None:
+            raise FFTError(fft_last_error(), "fft_plan_create_real")
+        self.numel = self.batch * int(n)
+
+    def forward(self, x, out=None):
+        import torch
+        n = self.lengths[0]
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.numel() != self.numel:
+            raise TypeError("forward input must be a contiguous CUDA float32 tensor of batch*n values")
+        if out is None:
+            out = torch.empty((self.batch, n // 2 + 1), dtype=torch.complex64, device=x.device)
+        s = torch.cuda.current_stream(x.device)
+        rc = fft_exec(self.handle, x.data_ptr(), out.data_ptr(), FFT_FORWARD, s.cuda_stream)
+        if rc != FFT_OK:
+            raise FFTError(rc, "fft_exec")
+        return out
+
+    def inverse(self, x, out=None):
+        import torch
+        n = self.lengths[0]
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous() or \
+                x.numel() != self.batch * (n // 2 + 1):
+            raise TypeError("inverse input must be a contiguous CUDA complex64 tensor [batch, n/2+1]")
+        if out is None:
+            out = torch.empty((self.batch, n), dtype=torch.float32, device=x.device)
+        s = torch.cuda.current_stream(x.device)
+        rc = fft_exec(self.handle, x.data_ptr(), out.data_ptr(), FFT_INVERSE, s.cuda_stream)
+        if rc != FFT_OK:
+            raise FFTError(rc, "fft_exec")
+        return out
+
+
+def convolve(x, h, corr: bool = False):
+    """Circular convolution (or correlation) of every row of x ([batch, n] or
+    [batch, H, W] complex64 on CUDA) with h ([n] or [H, W]): forward
+    transforms, the spectrum product with 1/N folded in, inverse transform --
+    all on the GPU through the C ABI."""
+    import torch
+    shape = tuple(x.shape[1:])
+    batch = x.shape[0]
+    n = 1
+    for v in shape:
+        n *= v
+    with Plan(shape, batch) as px, Plan(shape, 1) as ph:
+        X = px.forward(x)
+        H = ph.forward(h.reshape((1,) + shape).contiguous())
+        s = torch.cuda.current_stream(x.device)
+        rc = fft_spectrum_product(X.data_ptr(), H.data_ptr(), X.data_ptr(), n, batch, 1.0 / n, corr, s.cuda_stream)
+        if rc != FFT_OK:
+            raise FFTError(rc, "fft_spectrum_product")
+        return px.inverse(X)

@@ -1,0 +1,80 @@
+"""Real-to-complex / complex-to-real transforms and FFT convolution on the
+GPU against the FP64 oracle (needs a GPU).  Bar: relative L2 <= 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_4938_b300 import inputs
+from tests.gpu_util import TOL_FP32, cuda_or_skip, max_rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.mark.parametrize("n,batch", [(2, 3), (6, 5), (64, 7), (1000, 3), (4096, 9), (1 << 16, 3),
+                                     (2 * 1009, 2), (3 * 2 ** 13, 2), (1 << 20, 1)])
+def test_r2c_c2r(torch, n, batch):
+    from paper_1203_4938_b300 import fft as F
+    rng = np.random.default_rng(n + batch)
+    xr = rng.standard_normal((batch, n)).astype(np.float32)
+    ref = oracle.fft(xr.astype(np.complex128), -1)[:, : n // 2 + 1]
+    with F.RealPlan(n, batch) as p:
+        X = p.forward(torch.from_numpy(xr).cuda())
+        torch.cuda.synchronize()
+        assert max_rel_l2(X.cpu().numpy(), ref, -1) <= TOL_FP32
+        y = p.inverse(X)
+        torch.cuda.synchronize()
+        p.check()
+    assert max_rel_l2((y.cpu().numpy() / n).astype(np.complex128), xr.astype(np.complex128), -1) <= 2 * TOL_FP32
+
+
+def test_c2r_of_oracle_half_spectrum(torch):
+    """C2R alone, fed the oracle's half spectrum of a real signal."""
+    from paper_1203_4938_b300 import fft as F
+    n, batch = 4096, 4
+    xr = np.random.default_rng(3).uniform(-1, 1, (batch, n))
+    half = oracle.fft(xr.astype(np.complex128), -1)[:, : n // 2 + 1].astype(np.complex64)
+    with F.RealPlan(n, batch) as p:
+        y = p.inverse(to_dev(half))
+        torch.cuda.synchronize()
+    assert max_rel_l2(y.cpu().numpy().astype(np.complex128) / n, xr.astype(np.complex128), -1) <= 2 * TOL_FP32
+
+
+def test_real_plan_rejects_odd(torch):
+    from paper_1203_4938_b300 import fft as F
+    assert F.fft_plan_create_real(1001, 1) is None
+    assert F.fft_last_error() == F.FFT_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("n,batch", [(8, 3), (1024, 4), (1000, 2), (1 << 16, 2), (97, 3)])
+@pytest.mark.parametrize("corr", [False, True])
+def test_convolution_1d(torch, n, batch, corr):
+    from paper_1203_4938_b300 import fft as F
+    x = inputs.uniform_batch(batch, n, seed=n)
+    h = inputs.uniform_batch(1, n, seed=n + 1)[0]
+    y = F.convolve(to_dev(x), to_dev(h), corr).cpu().numpy()
+    ref = oracle.circ_conv(x, h, corr) if n <= 4096 else None
+    if ref is None:  # long signal: convolution theorem with the oracle's FFT
+        ref = oracle.fft(oracle.fft(x, -1) * (np.conj(oracle.fft(h, -1)) if corr else oracle.fft(h, -1)), +1) / n
+    assert max_rel_l2(y, ref, -1) <= 2 * TOL_FP32
+
+
+def test_convolution_2d_image_blur(torch):
+    """2-D circular filtering of image-shaped data (a 3x3 box kernel)."""
+    from paper_1203_4938_b300 import fft as F
+    hgt, wid = 64, 128
+    img = inputs.image_batch(np.random.default_rng(1), 2, hgt, wid)
+    k = np.zeros((hgt, wid), np.complex64)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            k[dy % hgt, dx % wid] = 1.0 / 9
+    y = F.convolve(to_dev(img), to_dev(k)).cpu().numpy()
+    ref = np.zeros_like(img, dtype=np.complex128)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            ref += np.roll(img.astype(np.complex128), (dy, dx), axis=(1, 2)) / 9
+    assert max_rel_l2(y.reshape(2, -1), ref.reshape(2, -1), -1) <= 2 * TOL_FP32
