@@ -439,6 +439,56 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+def run_real_conv(args):
+    """Real transforms and convolution: R2C then C2R of 2^27 real floats
+    (512 MiB) at N = 2^12, 2^16, 2^20, and FFT convolution of 2^14 signals of
+    4096 with one filter (forward, spectrum product, inverse); inputs normal(0,1)
+    from numpy seed 5."""
+    import torch
+    from paper_1203_4938_b300 import build as B
+    from paper_1203_4938_b300 import fft as F
+    B.build()
+    parts = {}
+    rng = np.random.default_rng(5)
+    for lg in (12, 16, 20):
+        n = 1 << lg
+        bt = (1 << 27) // n
+        x = torch.from_numpy(rng.standard_normal((bt, n), dtype=np.float32)).cuda()
+        p = F.RealPlan(n, bt)
+        X = torch.empty((bt, n // 2 + 1), dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        ms_f = _time_stream(lambda: p.forward(x, X), args.steps, args.warmup)
+        ms_i = _time_stream(lambda: p.inverse(X, y), args.steps, args.warmup)
+        # real input 4 B + half-spectrum output 8 B per (n/2+1) bins
+        byts = 4.0 * bt * n + 8.0 * bt * (n // 2 + 1)
+        parts[f"r2c N=2^{lg} x {bt}"] = {"us_fwd": ms_f * 1e3, "us_inv": ms_i * 1e3,
+                                          "gflops_fwd": bt * 2.5 * n * lg / (ms_f * 1e-3) / 1e9,
+                                          "effective_gbs_fwd": byts / (ms_f * 1e-3) / 1e9, "plan": p.describe()}
+        p.close()
+        del x, X, y
+    n, bt = 4096, 1 << 14
+    xs = torch.from_numpy(inputs.normal_batch(bt, n, seed=5)).cuda()
+    h = torch.from_numpy(inputs.normal_batch(1, n, seed=6)[0]).cuda()
+    px, ph = F.Plan((n,), bt), F.Plan((n,), 1)
+    H = ph.forward(h.reshape(1, n))
+    Xs = torch.empty_like(xs)
+    out = torch.empty_like(xs)
+
+    def conv():
+        px.forward(xs, Xs)
+        F.fft_spectrum_product(Xs.data_ptr(), H.data_ptr(), Xs.data_ptr(), n, bt, 1.0 / n, False,
+                               torch.cuda.current_stream().cuda_stream)
+        px.inverse(Xs, out)
+
+    ms = _time_stream(conv, args.steps, args.warmup)
+    parts[f"conv 1-D {bt} x {n}"] = {"us": ms * 1e3, "effective_gbs_3_passes": 3 * 16.0 * bt * n / (ms * 1e-3) / 1e9}
+    px.close()
+    ph.close()
+    print(json.dumps({"metric": "real transforms and FFT convolution", "parts": parts, "steps": args.steps,
+                      "warmup": args.warmup, "config": {"workload": "r2c/c2r 2^27 floats; conv 2^14 x 4096"}}),
+          flush=True)
+
+
 def run_case(args):
     """One plan run `steps` times (the small cases profiled with ncu):
     --case 1d|2d|ragged, --n (length, 2-D side, or ragged count), --batch,
@@ -467,7 +517,8 @@ def run_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "ragged", "image2d", "precision", "case"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "ragged", "image2d", "precision", "realconv", "case"])
     ap.add_argument("--case", default="1d", choices=["1d", "2d", "ragged"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--batch", type=int, default=1)
@@ -494,6 +545,8 @@ def main():
         run_precision(args)
     elif args.workload == "case":
         run_case(args)
+    elif args.workload == "realconv":
+        run_real_conv(args)
     else:
         run_gpu(args)
 
