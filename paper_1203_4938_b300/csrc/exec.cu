@@ -2,6 +2,7 @@
 #include "gplan.h"
 #include "launch.h"
 #include "persist.cuh"
+#include "threestep.cuh"
 #include "plan.h"
 
 namespace b300fft {
@@ -47,6 +48,36 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch), st);
             if (e == cudaSuccess)
                 e = launch_fourstep_persist(PersistConfig{p->pl1, p->pc, p->pl2, p->ptpc}, inv, a, p->pgrid, st);
+            break;
+        }
+        case PlanKind::ThreeStep: {
+            if (!want(0)) break;
+            ThreeArgs a;
+            a.in = in;
+            a.out = out;
+            a.work = p->d_work;
+            a.ctl = static_cast<int*>(p->d_aux);
+            a.status = p->d_status;
+            a.batch = p->batch;
+            a.cb = p->pcb;
+            a.nch = p->pnch;
+            a.na = p->pna;
+            a.nb = p->pnb;
+            a.G = p->pG;
+            a.nb1g = p->pnb1g;
+            a.nb2g = p->pnb2g;
+            a.D = p->pD;
+            a.tw_a = p->d_tables + p->off_a;
+            a.tw_b1 = p->d_tables + p->off_b;
+            a.tw_b2 = p->d_tables + p->off_c;
+            a.lo = p->d_tables + p->off_lo;
+            a.hi = p->d_tables + p->off_hi;
+            a.sh = p->sh;
+            a.spin_limit = p->spin_limit;
+            a.withhold_chunk = p->withhold_chunk;
+            e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch + (int64_t)p->pnch * p->pG), st);
+            if (e == cudaSuccess)
+                e = launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2}, inv, a, p->pgrid, st);
             break;
         }
         case PlanKind::TwoD: {

@@ -163,6 +163,95 @@ fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
     return FFT_OK;
 }
 
+// Persistent three-stage: N = N1 * M1 * M2 with 2^6 .. 2^8-point stages.
+// kThree[log2 N] = {log2 N1, log2 M1, log2 M2, chunk MiB, default on}.
+// Measured on a B300 with 2^26 elements per exec: faster than the two-pass
+// persistent four-step from 2^21 on (2^19 and 2^20 are slower).
+static const int kThree[25][5] = {
+    {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
+    {6, 6, 7, 128, 0}, {6, 7, 7, 128, 0}, {7, 7, 7, 128, 1}, {7, 7, 8, 128, 1},
+    {8, 7, 8, 32, 1}, {8, 8, 8, 32, 1}};
+
+bool three_preferred(int logn) { return logn >= 0 && logn <= 24 && kThree[logn][4] != 0; }
+
+fft_status build_threestep(fft_plan_s* p, int logn) {
+    const char* forced = std::getenv("B300FFT_THREE_CFG");
+    if (logn > 24 || (kThree[logn][0] == 0 && !forced)) return FFT_ERR_UNSUPPORTED;
+    ThreeConfig cfg{kThree[logn][0], kThree[logn][1], kThree[logn][2]};
+    if (forced) {
+        ThreeConfig o{};
+        if (std::sscanf(forced, "%d,%d,%d", &o.la, &o.lb1, &o.lb2) == 3 && o.la + o.lb1 + o.lb2 == logn) cfg = o;
+    }
+    if (cfg.la + cfg.lb1 + cfg.lb2 != logn || !three_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+    PersistInfo info;
+    if (three_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n = int64_t(1) << logn;
+    const int64_t n1 = int64_t(1) << cfg.la, m1 = int64_t(1) << cfg.lb1, m2 = int64_t(1) << cfg.lb2;
+    const int64_t n2 = m1 * m2;
+    const int64_t ca = 4096 >> cfg.la, cb_cols = 4096 >> cfg.lb1, tpc = 4096 >> cfg.lb2;
+    const int64_t chunk_bytes =
+        int64_t(env_int("B300FFT_CHUNK_MB", kThree[logn][3] ? kThree[logn][3] : 32)) << 20;
+    int64_t cb = chunk_bytes / (n * 8);
+    if (cb < 1) cb = 1;
+    if (cb > p->batch) cb = p->batch;
+    const int64_t nch = (p->batch + cb - 1) / cb;
+    const int64_t na = cb * (n2 / ca);
+    const int64_t G = cb * (n1 / tpc), nb1g = tpc * (m2 / cb_cols), nb2g = m1;
+    const int64_t nb = G * (nb1g + nb2g);
+    if (nch * (na + nb) > 0x7fffffffLL || nch * G > (1 << 26)) return FFT_ERR_UNSUPPORTED;
+    p->kind = PlanKind::ThreeStep;
+    p->pl1 = cfg.la;
+    p->pc = cfg.lb1;
+    p->pl2 = cfg.lb2;
+    p->pcb = cb;
+    p->pnch = (int)nch;
+    p->pna = (int)na;
+    p->pnb = (int)nb;
+    p->pG = (int)G;
+    p->pnb1g = (int)nb1g;
+    p->pnb2g = (int)nb2g;
+    const int64_t items = nch * (na + nb);
+    const int64_t slots = (int64_t)sms * info.blocks_per_sm;
+    p->pgrid = (int)(items < slots ? items : slots);
+    // B1 lookahead: at least twice the CTAs in flight between a B1 tile and its first consumer
+    int64_t D = (2 * (int64_t)p->pgrid + nb1g - 1) / nb1g;
+    D = env_int("B300FFT_THREE_LOOKAHEAD", (int)D);
+    if (D < 1) D = 1;
+    if (D > G) D = G;
+    p->pD = (int)D;
+    p->spin_limit = env_int("B300FFT_SPIN_LIMIT", 1 << 23);
+    p->withhold_chunk = env_int("B300FFT_DEBUG_WITHHOLD_CHUNK", -1);
+    p->sh = (logn + 1) / 2;
+    const size_t ea = (size_t)pow2_table_entries(cfg.la), eb = (size_t)pow2_table_entries(cfg.lb1),
+                 ec = (size_t)pow2_table_entries(cfg.lb2);
+    const size_t elo = size_t(1) << p->sh, ehi = size_t(1) << (logn - p->sh);
+    p->off_a = 0;
+    p->off_b = ea;
+    p->off_c = ea + eb;
+    p->off_lo = ea + eb + ec;
+    p->off_hi = p->off_lo + elo;
+    fft_status s = alloc_tables(p, p->off_hi + ehi);
+    if (s != FFT_OK) return s;
+    if (gen_pow2_table(p->d_tables + p->off_a, cfg.la, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_pow2_table(p->d_tables + p->off_b, cfg.lb1, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_pow2_table(p->d_tables + p->off_c, cfg.lb2, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_lo, (int64_t)elo, 1, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_hi, (int64_t)ehi, (int64_t)elo, n, 0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    p->work_bytes = (size_t)n * (size_t)p->batch * sizeof(float2);
+    if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (cudaMalloc(&p->d_aux, sizeof(int) * (size_t)(1 + nch + nch * G)) != cudaSuccess) return FFT_ERR_ALLOC;
+    p->kernels = 1;
+    std::snprintf(p->desc, sizeof p->desc,
+                  "threestep N=2^%d = 2^%d x (2^%d x 2^%d) threads=%d grid=%d chunk=%lld x %lld groups=%lld ahead=%lld",
+                  logn, cfg.la, cfg.lb1, cfg.lb2, info.threads, p->pgrid, (long long)cb, (long long)nch, (long long)G,
+                  (long long)D);
+    return FFT_OK;
+}
+
 fft_status build_pow2_1d(fft_plan_s* p, int logn) {
     p->single_max_log = env_int("B300FFT_SINGLE_MAX_LOG", p->single_max_log);
     if (logn <= p->single_max_log && logn <= kRowsMaxLog) {
@@ -178,6 +267,12 @@ fft_status build_pow2_1d(fft_plan_s* p, int logn) {
         std::snprintf(p->desc, sizeof p->desc, "rows N=2^%d tpc=%d threads=%d", logn, rows_tpc(logn),
                       rows_threads(logn));
         return FFT_OK;
+    }
+    // three-stage form where it is measured faster; B300FFT_THREE=1 forces it, 0 disables it
+    const int three = env_int("B300FFT_THREE", -1);
+    if (three == 1 || (three < 0 && three_preferred(logn))) {
+        fft_status ts = build_threestep(p, logn);
+        if (ts != FFT_ERR_UNSUPPORTED) return ts;
     }
     if (env_int("B300FFT_PERSIST", 1)) {
         fft_status ps = build_fourstep_persist(p, logn);

@@ -73,4 +73,14 @@ cudaError_t persist_prepare(const PersistConfig& c, PersistInfo* info);
 cudaError_t launch_fourstep_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid,
                                     cudaStream_t st);
 
+// --- persistent three-stage (k_three.cu) ------------------------------------
+// N = 2^la * 2^lb1 * 2^lb2, each stage length in 2^6 .. 2^8, 4096-point tiles.
+struct ThreeArgs;  // threestep.cuh
+struct ThreeConfig {
+    int la, lb1, lb2;
+};
+bool three_config_available(const ThreeConfig& c);
+cudaError_t three_prepare(const ThreeConfig& c, PersistInfo* info);
+cudaError_t launch_threestep(const ThreeConfig& c, bool inv, const ThreeArgs& a, int grid, cudaStream_t st);
+
 }  // namespace b300fft

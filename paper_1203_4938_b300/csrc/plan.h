@@ -14,6 +14,7 @@ enum class PlanKind : int {
     Rows,      // single-pass power-of-two rows kernel
     FourStep,  // columns + transposed rows, through the workspace
     FourStepPersist,  // both four-step passes in one persistent launch, L2-resident chunks
+    ThreeStep,        // three short-transform stages in one persistent launch (N = N1 * M1 * M2)
     TwoD,      // rows pass then in-place columns pass
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
@@ -48,7 +49,8 @@ struct fft_plan_s {
     int64_t pcb = 0;
     int64_t spin_limit = int64_t(1) << 23;
     int withhold_chunk = -1;
-    size_t off_a = 0, off_b = 0, off_lo = 0, off_hi = 0;  // into d_tables (float2 units)
+    int pG = 0, pnb1g = 0, pnb2g = 0, pD = 1;  // three-stage: groups per chunk, B1 / B2 tiles per group, lookahead
+    size_t off_a = 0, off_b = 0, off_c = 0, off_lo = 0, off_hi = 0;  // into d_tables (float2 units)
 
     float2* d_tables = nullptr;
     float2* d_work = nullptr;

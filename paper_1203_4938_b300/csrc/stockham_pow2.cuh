@@ -272,18 +272,16 @@ struct RowsTCfg {
     static constexpr int SMEM = PITCH * TPC * 8;
 };
 
-template <int LOGN, int TPC, bool INV, Ld LK, St SK>
-__device__ __forceinline__ void rowsT_tile(const float2* __restrict__ src, float2* __restrict__ dst, int64_t n1,
-                                           const float2* __restrict__ tw, float2* smem, uint64_t pol) {
+// Everything after the load: v holds x[t + i*T] of row `sub` (thread
+// (sub, t), t = threadIdx.x mod T).
+template <int LOGN, int TPC, bool INV, St SK>
+__device__ __forceinline__ void rowsT_tile_regs(float2 (&v)[P2Plan<LOGN>::R], float2* __restrict__ dst, int64_t n1,
+                                                const float2* __restrict__ tw, float2* smem, uint64_t pol) {
     using CF = RowsTCfg<LOGN, TPC>;
     using PL = typename CF::PL;
     static_assert(PL::NPASS >= 2, "transposed rows need at least two passes");
     const int t = threadIdx.x & (PL::T - 1);
     const int sub = threadIdx.x / PL::T;
-    const float2* s0 = src + (int64_t)sub * PL::N;
-    float2 v[PL::R];
-#pragma unroll
-    for (int i = 0; i < PL::R; ++i) v[i] = ldx<LK>(s0 + t + i * PL::T);
     run_passes_to_last<PL, 0, INV>(v, t, smem + sub * CF::PITCH, tw);
     const int c = threadIdx.x % TPC;
     const int t2 = threadIdx.x / TPC;
@@ -300,6 +298,18 @@ __device__ __forceinline__ void rowsT_tile(const float2* __restrict__ src, float
     float2* d0 = dst + c;
 #pragma unroll
     for (int i = 0; i < PL::R; ++i) stx<SK>(d0 + n1 * (int64_t)(t2 + i * PL::T), v[i], pol);
+}
+
+template <int LOGN, int TPC, bool INV, Ld LK, St SK>
+__device__ __forceinline__ void rowsT_tile(const float2* __restrict__ src, float2* __restrict__ dst, int64_t n1,
+                                           const float2* __restrict__ tw, float2* smem, uint64_t pol) {
+    using PL = P2Plan<LOGN>;
+    const int t = threadIdx.x & (PL::T - 1);
+    const float2* s0 = src + (int64_t)(threadIdx.x / PL::T) * PL::N;
+    float2 v[PL::R];
+#pragma unroll
+    for (int i = 0; i < PL::R; ++i) v[i] = ldx<LK>(s0 + t + i * PL::T);
+    rowsT_tile_regs<LOGN, TPC, INV, SK>(v, dst, n1, tw, smem, pol);
 }
 
 // Columns tile: C adjacent columns of a row-major [N][S] array (src/dst point
@@ -325,25 +335,23 @@ __device__ __forceinline__ float2 root2(const float2* __restrict__ lo, const flo
     return cmul(__ldg(hi + (m >> sh)), __ldg(lo + (m & ((1u << sh) - 1u))));
 }
 
-template <int LOGN, int C, bool INV, bool TW, Ld LK, St SK>
-__device__ __forceinline__ void cols_tile(const float2* __restrict__ src, float2* __restrict__ dst, int64_t S,
-                                          uint32_t col0, const float2* __restrict__ tw,
-                                          const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi, int sh,
-                                          float2* smem, uint64_t pol) {
+// Everything after the load: v holds x[t + i*T] of column c (thread (c, t)).
+// With TW the twiddle of element (k1, n2) is W^{tws*n2*k1} of the two-level
+// table (tws > 1 reuses a longer transform's table for a divisor length).
+template <int LOGN, int C, bool INV, bool TW, St SK>
+__device__ __forceinline__ void cols_tile_regs(float2 (&v)[P2Plan<LOGN>::R], float2* __restrict__ dst, int64_t S,
+                                               uint32_t col0, const float2* __restrict__ tw,
+                                               const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi,
+                                               int sh, float2* smem, uint64_t pol, uint32_t tws = 1) {
     using CF = ColsCfg<LOGN, C>;
     using PL = typename CF::PL;
     const int c = threadIdx.x % C;
     const int t = threadIdx.x / C;
-    src += c;
-    float2 v[PL::R];
-#pragma unroll
-    for (int i = 0; i < PL::R; ++i) v[i] = ldx<LK>(src + (int64_t)(t + i * PL::T) * S);
-
     float2* steps = smem + CF::XBUF;  // [R][C]: W^{n2*T*i} (column fastest: conflict-free reads)
     if constexpr (TW) {
         for (int j = threadIdx.x; j < C * PL::R; j += CF::THREADS) {
             const int cc = j % C, ii = j / C;
-            steps[ii * C + cc] = root2(tw_lo, tw_hi, (col0 + (uint32_t)cc) * (uint32_t)(ii * PL::T), sh);
+            steps[ii * C + cc] = root2(tw_lo, tw_hi, (col0 + (uint32_t)cc) * tws * (uint32_t)(ii * PL::T), sh);
         }
         if constexpr (PL::NPASS == 1) __syncthreads();
     }
@@ -351,13 +359,27 @@ __device__ __forceinline__ void cols_tile(const float2* __restrict__ src, float2
     run_passes<PL, 0, INV, false, C>(v, t, smem, c, tw);
 
     if constexpr (TW) {
-        const float2 w0 = root2(tw_lo, tw_hi, (col0 + (uint32_t)c) * (uint32_t)t, sh);
+        const float2 w0 = root2(tw_lo, tw_hi, (col0 + (uint32_t)c) * tws * (uint32_t)t, sh);
 #pragma unroll
         for (int i = 0; i < PL::R; ++i) v[i] = twmul<INV>(v[i], cmul(w0, steps[i * C + c]));
     }
     dst += c;
 #pragma unroll
     for (int i = 0; i < PL::R; ++i) stx<SK>(dst + (int64_t)(t + i * PL::T) * S, v[i], pol);
+}
+
+template <int LOGN, int C, bool INV, bool TW, Ld LK, St SK>
+__device__ __forceinline__ void cols_tile(const float2* __restrict__ src, float2* __restrict__ dst, int64_t S,
+                                          uint32_t col0, const float2* __restrict__ tw,
+                                          const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi, int sh,
+                                          float2* smem, uint64_t pol) {
+    using PL = P2Plan<LOGN>;
+    const int t = threadIdx.x / C;
+    src += threadIdx.x % C;
+    float2 v[PL::R];
+#pragma unroll
+    for (int i = 0; i < PL::R; ++i) v[i] = ldx<LK>(src + (int64_t)(t + i * PL::T) * S);
+    cols_tile_regs<LOGN, C, INV, TW, SK>(v, dst, S, col0, tw, tw_lo, tw_hi, sh, smem, pol);
 }
 
 // ---------------------------------------------------------------------------

@@ -172,30 +172,53 @@ def test_side_stream_and_graph_capture(torch):
     (20, {"B300FFT_PERSIST": "0"}),
     (17, {"B300FFT_CHUNK_MB": "1"}),                             # many chunks, ragged last chunk
     (18, {"B300FFT_PERSIST_CFG": "9,8,9,8", "B300FFT_CHUNK_MB": "3"}),
+    (18, {"B300FFT_PERSIST_CFG": "9,8,9,8", "B300FFT_CHUNK_MB": "64"}),  # one chunk: B tiles wait on A tiles
+    (22, {"B300FFT_PERSIST_CFG": "11,4,11,4", "B300FFT_CHUNK_MB": "16"}),
+    # three-stage persistent kernel (N = N1 * M1 * M2)
+    (19, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "6,6,7", "B300FFT_CHUNK_MB": "4"}),   # many chunks
+    (19, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "6,6,7", "B300FFT_CHUNK_MB": "64"}),  # one chunk
+    (20, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "7,7,6"}),
+    (20, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "6,7,7", "B300FFT_THREE_LOOKAHEAD": "1"}),
+    (21, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "7,7,7", "B300FFT_CHUNK_MB": "40"}),
+    (22, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "7,7,8"}),
+    (22, {"B300FFT_THREE": "0"}),                                # two-pass persistent instead
+    (23, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "8,7,8"}),
+    (23, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "7,8,8", "B300FFT_THREE_LOOKAHEAD": "64"}),
+    (24, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "8,8,8"}),
+    (24, {"B300FFT_THREE": "0"}),
 ])
 def test_fourstep_variants(torch, monkeypatch, logn, env):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     n = 1 << logn
-    batch = 5
+    batch = 5 if logn <= 21 else 2
     x = inputs.normal_batch(batch, n, seed=logn + 50)
     for d in (-1, +1):
         y = run((n,), batch, x, d)
         assert max_rel_l2(y, oracle.fft(x, d), -1) <= TOL_FP32, (logn, env, d)
 
 
-def test_persistent_wait_timeout_is_reported(torch, monkeypatch):
+@pytest.mark.parametrize("cfg", [None, "8,8,8,8", "three"])
+def test_persistent_wait_timeout_is_reported(torch, monkeypatch, cfg):
     """A chunk counter that nothing ever completes makes the bounded waits of
     the second-pass tiles expire: the kernel returns, the plan reports
-    FFT_ERR_TIMEOUT, and the device stays usable for the next plan."""
+    FFT_ERR_TIMEOUT, and the device stays usable for the next plan (default
+    four-step tiles, 128-thread tiles and the three-stage kernel)."""
     from paper_1203_4938_b300 import fft as F
     n, b = 1 << 16, 8
     x = to_dev(inputs.uniform_batch(b, n, seed=9))
+    if cfg == "three":
+        n = 1 << 19
+        x = to_dev(inputs.uniform_batch(b, n, seed=9))
+        monkeypatch.setenv("B300FFT_THREE", "1")
+        monkeypatch.setenv("B300FFT_THREE_CFG", "6,6,7")
+    elif cfg:
+        monkeypatch.setenv("B300FFT_PERSIST_CFG", cfg)
     monkeypatch.setenv("B300FFT_DEBUG_WITHHOLD_CHUNK", "0")
     monkeypatch.setenv("B300FFT_SPIN_LIMIT", "20000")
     monkeypatch.setenv("B300FFT_CHUNK_MB", "1")
     with F.Plan((n,), b) as p:
-        assert "persist" in p.describe()
+        assert ("threestep" if cfg == "three" else "persist") in p.describe()
         p.forward(x)
         torch.cuda.synchronize()
         assert F.fft_plan_check(p.handle) == F.FFT_ERR_TIMEOUT
