@@ -10,6 +10,9 @@ sequence, ``X[k] = sum_n x[n] exp(sign*2*pi*i*n*k/N)`` with sign -1 for the
 forward and +1 for the inverse transform, both unnormalised; the paper
 computes it with radix-2 Cooley-Tukey, which ``fft`` follows for powers of two.
 
+``image_steps`` follows the image example of Sec. III-B (its GPU steps 1-3:
+colour transform, chroma downscale, directional derivative of luminance).
+
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, textbook values in ``tests/golden/``, Parseval, linearity,
 shift, symmetry, brute force and an independent library witness); planted
@@ -85,6 +88,9 @@ class OracleLib:
                                      ctypes.c_int]
         lib.oracle_circ_conv.argtypes = [dp, dp, dp, i64, ctypes.c_int]
         lib.oracle_circ_conv.restype = ctypes.c_int
+        lib.oracle_image_steps.argtypes = [ctypes.c_void_p, i64, i64, i64, ctypes.c_double, ctypes.c_double,
+                                           dp, dp, dp, dp]
+        lib.oracle_image_steps.restype = ctypes.c_int
         lib.oracle_num_cpus.argtypes = []
         for f in ("oracle_dft_naive", "oracle_dft_bins", "oracle_fft_radix2",
                   "oracle_fft_split_m", "oracle_fft", "oracle_fft_batch",
@@ -153,6 +159,21 @@ class OracleLib:
                    "circ_conv")
         return y.reshape(x.shape)
 
+    def image_steps(self, rgb, ux: float = 1.0, uy: float = 0.0):
+        """Steps 1-3 of the image example (Sec. III-B): YCbCr, chroma 2x2 mean,
+        directional derivative of Y.  rgb: uint8 [batch, h, w, 3].  Returns
+        (y, cb, cr, d) in FP64: y, d [batch, h, w]; cb, cr [batch, h/2, w/2]."""
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        b, h, w, c = rgb.shape
+        assert c == 3
+        y = np.empty((b, h, w))
+        d = np.empty((b, h, w))
+        cb = np.empty((b, h // 2, w // 2))
+        cr = np.empty((b, h // 2, w // 2))
+        _check(self.lib.oracle_image_steps(rgb.ctypes.data_as(ctypes.c_void_p), b, h, w, float(ux), float(uy),
+                                           _ptr(y), _ptr(cb), _ptr(cr), _ptr(d)), "image_steps")
+        return y, cb, cr, d
+
     def fft2(self, x, sign: int = FORWARD, threads: int = 0) -> np.ndarray:
         """2-D DFT over the last two axes: rows first, then columns."""
         x = _c128(x)
@@ -204,6 +225,10 @@ def fft2(x, sign: int = FORWARD, threads: int = 0) -> np.ndarray:
 
 def circ_conv(x, h, corr: bool = False) -> np.ndarray:
     return default().circ_conv(x, h, corr)
+
+
+def image_steps(rgb, ux: float = 1.0, uy: float = 0.0):
+    return default().image_steps(rgb, ux, uy)
 
 
 def rel_l2(y, ref) -> np.ndarray:

@@ -318,3 +318,48 @@ int oracle_circ_conv(const double *x, const double *h, double *y, int64_t n, int
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Image example, Sec. III-B, GPU steps 1-3 (the paper names the steps but   */
+/* not their formulas; readings):                                           */
+/*  1. chroma + luminance: JFIF (ITU-R BT.601 full range) YCbCr of 8-bit    */
+/*     RGB,  Y = .299 R + .587 G + .114 B,                                  */
+/*     Cb = 128 - .168736 R - .331264 G + .5 B,                              */
+/*     Cr = 128 + .5 R - .418688 G - .081312 B;                              */
+/*  2. chroma downscaled to 1/4 of the pixels: mean of each 2x2 block;      */
+/*  3. directional derivative of Y along the unit vector (ux, uy):          */
+/*     ux dY/dx + uy dY/dy, central differences inside the image and        */
+/*     one-sided first differences on its border.                           */
+/* rgb: batch x h x w x 3 bytes; y, d: batch x h x w; cb, cr: batch x       */
+/* (h/2) x (w/2).  h, w even and >= 2.                                      */
+/* ------------------------------------------------------------------------ */
+static double deriv_1d(const double *v, int64_t i, int64_t n, int64_t stride)
+{
+    if (i == 0) return v[stride] - v[0];
+    if (i == n - 1) return v[(n - 1) * stride] - v[(n - 2) * stride];
+    return 0.5 * (v[(i + 1) * stride] - v[(i - 1) * stride]);
+}
+
+int oracle_image_steps(const unsigned char *rgb, int64_t batch, int64_t h, int64_t w, double ux, double uy,
+                       double *y, double *cb, double *cr, double *d)
+{
+    if (batch < 0 || h < 2 || w < 2 || (h & 1) || (w & 1)) return -1;
+    const int64_t hw = h * w, q = (h / 2) * (w / 2);
+    for (int64_t b = 0; b < batch; ++b) {
+        const unsigned char *img = rgb + b * hw * 3;
+        double *yb = y + b * hw, *db = d + b * hw, *cbb = cb + b * q, *crb = cr + b * q;
+        for (int64_t i = 0; i < q; ++i) cbb[i] = crb[i] = 0.0;
+        for (int64_t r = 0; r < h; ++r)
+            for (int64_t c = 0; c < w; ++c) {
+                const double R = img[3 * (r * w + c)], G = img[3 * (r * w + c) + 1], B = img[3 * (r * w + c) + 2];
+                yb[r * w + c] = 0.299 * R + 0.587 * G + 0.114 * B;
+                const int64_t k = (r / 2) * (w / 2) + c / 2;
+                cbb[k] += 0.25 * (128.0 - 0.168736 * R - 0.331264 * G + 0.5 * B);
+                crb[k] += 0.25 * (128.0 + 0.5 * R - 0.418688 * G - 0.081312 * B);
+            }
+        for (int64_t r = 0; r < h; ++r)
+            for (int64_t c = 0; c < w; ++c)
+                db[r * w + c] = ux * deriv_1d(yb + r * w, c, w, 1) + uy * deriv_1d(yb + c, r, h, w);
+    }
+    return 0;
+}

@@ -282,10 +282,103 @@ def pin_convolution(o):
            np.array([5, 3, 5, 7], complex), 1e-14, "conv 4-point")
 
 
+# --------------------------------------------------------------------------
+# image example (Sec. III-B) steps 1-3: colour transform, chroma 2x2 mean,
+# directional derivative of luminance
+# --------------------------------------------------------------------------
+def _rgb(b, h, w, seed):
+    return _rng(seed).integers(0, 256, (b, h, w, 3)).astype(np.uint8)
+
+
+def pin_ycc_gray(o):
+    """Gray pixels (R = G = B = v) have Y = v and no colour: Cb = Cr = 128."""
+    v = np.arange(0, 256, 5, dtype=np.uint8)
+    rgb = np.repeat(np.repeat(v[:, None, None, None], 4, 1), 6, 2).repeat(3, 3)
+    y, cb, cr, _ = o.image_steps(rgb)
+    _close(y, np.broadcast_to(v[:, None, None].astype(float), y.shape), 1e-12, "gray luma")
+    _close(cb, np.full(cb.shape, 128.0), 1e-12, "gray Cb")
+    _close(cr, np.full(cr.shape, 128.0), 1e-12, "gray Cr")
+
+
+def pin_ycc_inverse(o):
+    """The published JFIF inverse (R = Y + 1.402 (Cr-128), G = Y - 0.344136
+    (Cb-128) - 0.714136 (Cr-128), B = Y + 1.772 (Cb-128)) recovers every colour
+    (constant 2x2 images, so the downscaled chroma is the pixel's chroma)."""
+    cols = _rgb(1, 1, 300, 40)[0, 0]
+    rgb = np.repeat(np.repeat(cols[:, None, None, :], 2, 1), 2, 2)
+    y, cb, cr, _ = o.image_steps(rgb)
+    Y, Cb, Cr = y[:, 0, 0], cb[:, 0, 0] - 128.0, cr[:, 0, 0] - 128.0
+    back = np.stack([Y + 1.402 * Cr, Y - 0.344136 * Cb - 0.714136 * Cr, Y + 1.772 * Cb], 1)
+    err = float(np.max(np.abs(back - cols.astype(float))))
+    assert err <= 2e-3, f"JFIF inverse misses the colour by {err:.3e}"
+
+
+def pin_ycc_colour_difference(o):
+    """BT.601 colour differences: Cb - 128 = (B - Y) / (2 (1 - 0.114)) and
+    Cr - 128 = (R - Y) / (2 (1 - 0.299))."""
+    cols = _rgb(1, 1, 200, 41)[0, 0].astype(np.uint8)
+    rgb = np.repeat(np.repeat(cols[:, None, None, :], 2, 1), 2, 2)
+    y, cb, cr, _ = o.image_steps(rgb)
+    Y = y[:, 0, 0]
+    R, B = cols[:, 0].astype(float), cols[:, 2].astype(float)
+    assert float(np.max(np.abs(cb[:, 0, 0] - 128.0 - (B - Y) / 1.772))) <= 2e-3, "Cb colour difference"
+    assert float(np.max(np.abs(cr[:, 0, 0] - 128.0 - (R - Y) / 1.402))) <= 2e-3, "Cr colour difference"
+
+
+def pin_chroma_block_mean(o):
+    """Downscaled chroma = mean over each 2x2 block of the chroma of its four
+    pixel colours (each taken from a constant 2x2 image)."""
+    rgb = _rgb(2, 6, 8, 42)
+    _, cb, cr, _ = o.image_steps(rgb)
+    for b in range(2):
+        for j in range(3):
+            for i in range(4):
+                px = rgb[b, 2 * j:2 * j + 2, 2 * i:2 * i + 2].reshape(4, 3)
+                one = np.repeat(np.repeat(px[:, None, None, :], 2, 1), 2, 2)
+                _, cbs, crs, _ = o.image_steps(one)
+                assert abs(cb[b, j, i] - cbs.mean()) <= 1e-9, ("Cb block", b, j, i)
+                assert abs(cr[b, j, i] - crs.mean()) <= 1e-9, ("Cr block", b, j, i)
+
+
+def pin_derivative_closed_forms(o):
+    """Gray ramps: Y = a x + b y + c has directional derivative ux a + uy b
+    everywhere (central differences inside, one-sided on the border, both
+    exact for a linear function); Y = x^2 has 2x inside, 1 and 2w - 3 on the
+    left and right borders; a constant has 0."""
+    h, w = 6, 10
+    yy, xx = np.mgrid[0:h, 0:w]
+    for a, bb, c, ux, uy in ((3, 7, 11, 1.0, 0.0), (3, 7, 11, 0.0, 1.0), (5, 2, 9, 0.6, 0.8),
+                             (-4, 9, 200, -0.8, 0.6)):
+        g = (a * xx + bb * yy + c).astype(np.uint8)
+        rgb = np.repeat(g[None, :, :, None], 3, 3)
+        y, _, _, d = o.image_steps(rgb, ux, uy)
+        _close(y[0], g.astype(float), 1e-12, "ramp luma")
+        _close(d[0], np.full((h, w), ux * a + uy * bb), 1e-12, f"ramp derivative {(a, bb, ux, uy)}")
+    g = (xx ** 2).astype(np.uint8)
+    _, _, _, d = o.image_steps(np.repeat(g[None, :, :, None], 3, 3), 1.0, 0.0)
+    want = 2.0 * xx.astype(float)
+    want[:, 0] = 1.0
+    want[:, w - 1] = 2 * w - 3
+    _close(d[0], want, 1e-12, "quadratic derivative")
+    _, _, _, d = o.image_steps(np.full((1, 4, 4, 3), 77, np.uint8), 0.6, 0.8)
+    _close(d, np.zeros_like(d), 1e-12, "constant derivative")
+
+
+def pin_derivative_linear_in_direction(o):
+    """D(ux, uy) = ux D(1, 0) + uy D(0, 1) on random images."""
+    rgb = _rgb(2, 8, 12, 43)
+    _, _, _, dx = o.image_steps(rgb, 1.0, 0.0)
+    _, _, _, dy = o.image_steps(rgb, 0.0, 1.0)
+    _, _, _, du = o.image_steps(rgb, 0.28, -0.96)
+    _close(du, 0.28 * dx - 0.96 * dy, 1e-12, "derivative linearity")
+
+
 ALL_PINS = [pin_golden, pin_impulse, pin_shifted_impulse, pin_constant, pin_tone,
             pin_parseval, pin_linearity, pin_shift, pin_conjugate_symmetry,
             pin_round_trip, pin_brute_force, pin_batch, pin_library_witness,
-            pin_2d, pin_image_dc_and_spikes, pin_convolution]
+            pin_2d, pin_image_dc_and_spikes, pin_convolution,
+            pin_ycc_gray, pin_ycc_inverse, pin_ycc_colour_difference, pin_chroma_block_mean,
+            pin_derivative_closed_forms, pin_derivative_linear_in_direction]
 
 
 def failing_pins(o):

@@ -41,6 +41,19 @@ MUTANTS = [
     ("corr_missing_conj", "hr = h[2 * j]; hi = -h[2 * j + 1];", "hr = h[2 * j]; hi = h[2 * j + 1];"),
     ("2d_rows_only", "rc = oracle_fft_batch(col, fc, h, w, sign, nthreads);",
      "memcpy(fc, col, sizeof(double) * 2 * (size_t)(h * w)); rc = 0;"),
+    ("ycc_luma_weight", "0.299 * R + 0.587 * G + 0.114 * B", "0.299 * R + 0.578 * G + 0.114 * B"),
+    ("ycc_cb_sign", "128.0 - 0.168736 * R - 0.331264 * G + 0.5 * B", "128.0 - 0.168736 * R + 0.331264 * G + 0.5 * B"),
+    ("ycc_cr_offset", "0.25 * (128.0 + 0.5 * R", "0.25 * (0.0 + 0.5 * R"),
+    ("ycc_cb_cr_swapped", "0.25 * (128.0 - 0.168736 * R - 0.331264 * G + 0.5 * B)",
+     "0.25 * (128.0 + 0.5 * R - 0.418688 * G - 0.081312 * B)"),
+    ("chroma_half_weight", "cbb[k] += 0.25 *", "cbb[k] += 0.5 *"),
+    ("chroma_wrong_block", "const int64_t k = (r / 2) * (w / 2) + c / 2;",
+     "const int64_t k = (r / 2) * (w / 2) + c % (w / 2);"),
+    ("deriv_border_central", "if (i == 0) return v[stride] - v[0];", "if (i == 0) return 0.5 * (v[stride] - v[0]);"),
+    ("deriv_axes_swapped", "ux * deriv_1d(yb + r * w, c, w, 1) + uy * deriv_1d(yb + c, r, h, w)",
+     "uy * deriv_1d(yb + r * w, c, w, 1) + ux * deriv_1d(yb + c, r, h, w)"),
+    ("deriv_sign", "return 0.5 * (v[(i + 1) * stride] - v[(i - 1) * stride]);",
+     "return 0.5 * (v[(i - 1) * stride] - v[(i + 1) * stride]);"),
 ]
 
 
