@@ -444,6 +444,64 @@ def run_image2d(args):
     print(json.dumps(line), flush=True)
 
 
+def run_image_steps(args):
+    """Image example steps 1-3 (Sec. III-B), fused: RGB -> YCbCr, chroma 2x2
+    means, directional derivative of Y along (1, 1)/sqrt(2); RGB images of
+    the 2-D workload's shapes (one 4096^2, 16 x 2048^2), seed 2.  HBM bytes
+    per pixel: 3 in, 4 (Y) + 4 (derivative) + 2 (Cb, Cr at a quarter) out."""
+    import torch
+    from paper_1203_4938_b300 import build as B
+    from paper_1203_4938_b300 import fft as F
+    B.build()
+    a, b = inputs.rgb_workload(seed=2)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    u = 1.0 / math.sqrt(2.0)
+    devs = [(name, torch.from_numpy(arr).cuda()) for name, arr in (("4096x4096", a), ("16x2048x2048", b))]
+    outs = {name: (torch.empty(x.shape[:3], device="cuda"), torch.empty((x.shape[0], x.shape[1] // 2, x.shape[2] // 2),
+                                                                      device="cuda"),
+                   torch.empty((x.shape[0], x.shape[1] // 2, x.shape[2] // 2), device="cuda"),
+                   torch.empty(x.shape[:3], device="cuda")) for name, x in devs}
+    parts, tot_ms, tot_px = {}, 0.0, 0
+    for name, x in devs:
+        px = x.shape[0] * x.shape[1] * x.shape[2]
+        ms = _time_stream(lambda: F.image_steps(x, u, u, outs[name]), args.steps, args.warmup)
+        parts[name] = {"ms": ms, "mpix_per_s": px / (ms * 1e-3) / 1e6, "effective_gbs": 13.0 * px / (ms * 1e-3) / 1e9}
+        tot_ms += ms
+        tot_px += px
+    achieved = 13.0 * tot_px / (tot_ms * 1e-3) / 1e9
+    # end to end: pinned host RGB -> device, kernel, all four outputs -> pinned host
+    hin = [torch.from_numpy(arr).pin_memory() for arr in (a, b)]
+    hout = {name: tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs[name]) for name, _ in devs}
+
+    def e2e_step():
+        for (name, x), h in zip(devs, hin):
+            x.copy_(h, non_blocking=True)
+            F.image_steps(x, u, u, outs[name])
+            for t, ht in zip(outs[name], hout[name]):
+                ht.copy_(t, non_blocking=True)
+
+    ems = _time_stream(e2e_step, max(1, args.steps // 4), 1)
+    line = {"metric": "image steps 1-3 (YCbCr, chroma 2x2, directional derivative) Mpixel/s",
+            "value": tot_px / (tot_ms * 1e-3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "RGB 1x4096^2 + 16x2048^2, seed 2", "direction": "(1,1)/sqrt(2)"},
+            "gpu_launches": args.steps * len(devs),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes_per_pixel": 13,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                         else "fallback 6.4 TB/s"},
+            "e2e": {"value": tot_px / (ems * 1e-3) / 1e6, "unit": "Mpixel/s", "ms_per_step": ems,
+                    "h2d_bytes_per_step": 3 * tot_px, "d2h_bytes_per_step": 10 * tot_px},
+            "parts": parts}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     """Precision forms: batch 4096 x N=4096 and 256 x N=65536, normal(0,1)
     seed 3; FP32 Stockham vs tensor-core radix-16 (FP16/BF16, hi+lo and
@@ -555,7 +613,7 @@ def run_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "ragged", "image2d", "precision", "realconv", "case"])
+                    choices=["sweep", "ragged", "image2d", "imagesteps", "precision", "realconv", "case"])
     ap.add_argument("--case", default="1d", choices=["1d", "2d", "ragged"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--batch", type=int, default=1)
@@ -578,6 +636,8 @@ def main():
         run_ragged(args)
     elif args.workload == "image2d":
         run_image2d(args)
+    elif args.workload == "imagesteps":
+        run_image_steps(args)
     elif args.workload == "precision":
         run_precision(args)
     elif args.workload == "case":

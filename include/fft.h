@@ -117,6 +117,22 @@ FFT_API fft_plan fft_plan_create_real(int64_t n, int64_t batch);
 FFT_API fft_status fft_spectrum_product(const void *a, const void *b, void *out, int64_t n, int64_t batch,
                                         float scale, int conj_b, void *stream);
 
+/* The GPU steps of the image example (Sec. III-B), fused in one pass (no
+ * paper formulas are given; the readings below are the standard ones):
+ *   1. JFIF (ITU-R BT.601 full range) YCbCr of 8-bit RGB:
+ *        Y = .299 R + .587 G + .114 B, Cb = 128 - .168736 R - .331264 G + .5 B,
+ *        Cr = 128 + .5 R - .418688 G - .081312 B;
+ *   2. Cb, Cr downscaled to a quarter of the pixels (mean of each 2x2 block);
+ *   3. directional derivative of Y along (ux, uy): ux dY/dx + uy dY/dy with
+ *      central differences inside, one-sided first differences on the border.
+ * rgb: [batch][h][w][3] uint8 (interleaved R, G, B), 2-byte aligned;
+ * y, d: [batch][h][w] float32; cb, cr: [batch][h/2][w/2] float32, 4-byte
+ * aligned; device pointers (misaligned: FFT_ERR_MISALIGNED).
+ * h, w even, 2 <= h <= 2^19, 2 <= w <= 2^24, batch <= 65535 (else
+ * FFT_ERR_INVALID_ARG).  Asynchronous on `stream`; allocates nothing. */
+FFT_API fft_status fft_image_steps(const void *rgb, int64_t batch, int64_t h, int64_t w, float ux, float uy,
+                                   void *y, void *cb, void *cr, void *d, void *stream);
+
 /* Status of the last fft_plan_create* call on this host thread. */
 FFT_API fft_status fft_last_error(void);
 

@@ -42,7 +42,7 @@ PRECISIONS = {"fp32": FFT_FP32, "tc_fp16": FFT_TC_FP16, "tc_bf16": FFT_TC_BF16,
 EXPORTS = ("fft_plan_create", "fft_plan_create_ragged", "fft_last_error", "fft_exec",
            "fft_plan_check", "fft_plan_destroy", "fft_plan_workspace_bytes", "fft_status_string",
            "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size",
-           "fft_exec_pow2_static", "fft_plan_create_real", "fft_spectrum_product")
+           "fft_exec_pow2_static", "fft_plan_create_real", "fft_spectrum_product", "fft_image_steps")
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +73,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fft_spectrum_product.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                              ctypes.c_int, vp]
         lib.fft_spectrum_product.restype = ctypes.c_int
+        lib.fft_image_steps.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                                        ctypes.c_float, vp, vp, vp, vp, vp]
+        lib.fft_image_steps.restype = ctypes.c_int
         lib.fft_plan_create_real.argtypes = [ctypes.c_int64, ctypes.c_int64]
         lib.fft_plan_create_real.restype = vp
         lib.fft_last_error.argtypes = []
@@ -129,6 +132,12 @@ def fft_spectrum_product(a_ptr: int, b_ptr: int, out_ptr: int, n: int, batch: in
                          conj_b: bool = False, stream: int = 0) -> int:
     return int(load().fft_spectrum_product(a_ptr, b_ptr, out_ptr, int(n), int(batch), float(scale),
                                            int(bool(conj_b)), stream or None))
+
+
+def fft_image_steps(rgb_ptr: int, batch: int, h: int, w: int, ux: float, uy: float, y_ptr: int, cb_ptr: int,
+                    cr_ptr: int, d_ptr: int, stream: int = 0) -> int:
+    return int(load().fft_image_steps(rgb_ptr, int(batch), int(h), int(w), float(ux), float(uy), y_ptr, cb_ptr,
+                                      cr_ptr, d_ptr, stream or None))
 
 
 def fft_last_error() -> int:
@@ -366,3 +375,27 @@ def convolve(x, h, corr: bool = False):
         if rc != FFT_OK:
             raise FFTError(rc, "fft_spectrum_product")
         return px.inverse(X)
+
+
+def image_steps(rgb, ux: float = 1.0, uy: float = 0.0, out=None):
+    """Steps 1-3 of the image example on the GPU: rgb is a [batch, h, w, 3]
+    uint8 CUDA tensor (h, w even).  Returns (y, cb, cr, d) float32 tensors:
+    luminance and its directional derivative along (ux, uy) at full size,
+    chroma at half width and half height.  ``out`` may supply the four
+    output tensors."""
+    import torch
+    if rgb.dtype != torch.uint8 or not rgb.is_cuda or not rgb.is_contiguous() or rgb.dim() != 4 or rgb.shape[3] != 3:
+        raise TypeError("rgb must be a contiguous CUDA uint8 tensor of shape [batch, h, w, 3]")
+    b, h, w, _ = rgb.shape
+    if out is None:
+        out = (torch.empty((b, h, w), dtype=torch.float32, device=rgb.device),
+               torch.empty((b, h // 2, w // 2), dtype=torch.float32, device=rgb.device),
+               torch.empty((b, h // 2, w // 2), dtype=torch.float32, device=rgb.device),
+               torch.empty((b, h, w), dtype=torch.float32, device=rgb.device))
+    y, cb, cr, d = out
+    s = torch.cuda.current_stream(rgb.device)
+    rc = fft_image_steps(rgb.data_ptr(), b, h, w, ux, uy, y.data_ptr(), cb.data_ptr(), cr.data_ptr(), d.data_ptr(),
+                         s.cuda_stream)
+    if rc != FFT_OK:
+        raise FFTError(rc, "fft_image_steps")
+    return y, cb, cr, d

@@ -130,6 +130,29 @@ def ragged_lengths(count: int = 10000, seed: int = 4):
     return out, rng
 
 
+def rgb_images(rng: np.random.Generator, batch: int, h: int, w: int) -> np.ndarray:
+    """[batch][h][w][3] uint8 RGB images: per channel a smooth field
+    (128 + 100 sin/cos with integer periods, different per channel) plus
+    uniform noise in [-24, 24], clipped to 0..255."""
+    y = np.arange(h, dtype=np.float32)[:, None] / h
+    x = np.arange(w, dtype=np.float32)[None, :] / w
+    fields = (np.sin(2 * np.pi * (3 * x + 2 * y)), np.cos(2 * np.pi * (2 * x - y)), np.sin(2 * np.pi * (x + 4 * y)))
+    out = np.empty((batch, h, w, 3), dtype=np.uint8)
+    for c in range(3):
+        base = 128.0 + 100.0 * fields[c]
+        for b in range(batch):
+            v = base + rng.integers(-24, 25, (h, w)).astype(np.float32)
+            out[b, :, :, c] = np.clip(v, 0, 255).astype(np.uint8)
+    return out
+
+
+def rgb_workload(seed: int = 2, big: int = 4096, small: int = 2048, nsmall: int = 16):
+    """The image-example workload in RGB: one big x big and nsmall small x
+    small images (the shapes of the 2-D FFT workload), seeded."""
+    rng = np.random.default_rng(seed)
+    return rgb_images(rng, 1, big, big), rgb_images(rng, nsmall, small, small)
+
+
 def ragged_workload(count: int = 10000, seed: int = 4):
     """(lengths, offsets, packed complex64 data) for the ragged batch.
 
