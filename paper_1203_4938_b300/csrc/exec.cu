@@ -80,6 +80,11 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                 e = launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2}, inv, a, p->pgrid, st);
             break;
         }
+        case PlanKind::Cluster:
+            if (want(0))
+                e = launch_cluster_fft(p->cl_lm, p->cl_k, inv, in, out, p->batch, p->d_tables + p->off_a,
+                                       p->d_tables + p->off_lo, p->d_tables + p->off_hi, p->sh, st);
+            break;
         case PlanKind::TwoD: {
             const int64_t h = p->len[0], w = p->len[1];
             if (want(0)) e = launch_rows(p->logn_a, inv, in, out, p->batch * h, p->d_tables + p->off_a, st);

@@ -252,6 +252,53 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     return FFT_OK;
 }
 
+// Thread-block-cluster single pass: N = K * 2^lm, one transform per cluster.
+// kCluster[log2 N] = {lm, K, default on}.
+static const int kCluster[18][3] = {{0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
+                                    {12, 8, 0}, {13, 8, 0}, {14, 8, 0}};
+
+fft_status build_cluster(fft_plan_s* p, int logn, bool forced) {
+    if (logn < 15 || logn > 17) return FFT_ERR_UNSUPPORTED;
+    int lm = kCluster[logn][0], k = kCluster[logn][1];
+    if (!forced && !kCluster[logn][2]) return FFT_ERR_UNSUPPORTED;
+    if (const char* v = std::getenv("B300FFT_CLUSTER_CFG")) {
+        int a = 0, b = 0;
+        if (std::sscanf(v, "%d,%d", &a, &b) == 2 && (int64_t(b) << a) == (int64_t(1) << logn)) {
+            lm = a;
+            k = b;
+        }
+    }
+    if (!cluster_config_available(lm, k) || (int64_t(k) << lm) != (int64_t(1) << logn)) return FFT_ERR_UNSUPPORTED;
+    if ((int64_t)k * p->batch > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+    int clusters = 0;
+    if (cluster_prepare(lm, k, &clusters) != cudaSuccess) {
+        cudaGetLastError();
+        return FFT_ERR_UNSUPPORTED;
+    }
+    if (clusters < 1) return FFT_ERR_UNSUPPORTED;
+    p->kind = PlanKind::Cluster;
+    p->cl_lm = lm;
+    p->cl_k = k;
+    p->sh = (logn + 1) / 2;
+    const int64_t n = int64_t(1) << logn;
+    const size_t ea = (size_t)pow2_table_entries(lm);
+    const size_t elo = size_t(1) << p->sh, ehi = size_t(1) << (logn - p->sh);
+    p->off_a = 0;
+    p->off_lo = ea;
+    p->off_hi = ea + elo;
+    fft_status s = alloc_tables(p, p->off_hi + ehi);
+    if (s != FFT_OK) return s;
+    if (gen_pow2_table(p->d_tables + p->off_a, lm, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_lo, (int64_t)elo, 1, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_hi, (int64_t)ehi, (int64_t)elo, n, 0) != cudaSuccess)
+        return FFT_ERR_CUDA;
+    p->kernels = 1;
+    std::snprintf(p->desc, sizeof p->desc,
+                  "cluster N=2^%d = %d CTAs x 2^%d (DSMEM exchange) threads=%d co-resident clusters=%d", logn, k, lm,
+                  (1 << lm) / 16, clusters);
+    return FFT_OK;
+}
+
 fft_status build_pow2_1d(fft_plan_s* p, int logn) {
     p->single_max_log = env_int("B300FFT_SINGLE_MAX_LOG", p->single_max_log);
     if (logn <= p->single_max_log && logn <= kRowsMaxLog) {
@@ -267,6 +314,14 @@ fft_status build_pow2_1d(fft_plan_s* p, int logn) {
         std::snprintf(p->desc, sizeof p->desc, "rows N=2^%d tpc=%d threads=%d", logn, rows_tpc(logn),
                       rows_threads(logn));
         return FFT_OK;
+    }
+    // cluster single pass where it is measured faster; B300FFT_CLUSTER=1 forces it, 0 disables it
+    {
+        const int cl = env_int("B300FFT_CLUSTER", -1);
+        if (cl != 0) {
+            fft_status cs = build_cluster(p, logn, cl == 1);
+            if (cs != FFT_ERR_UNSUPPORTED) return cs;
+        }
     }
     // three-stage form where it is measured faster; B300FFT_THREE=1 forces it, 0 disables it
     const int three = env_int("B300FFT_THREE", -1);

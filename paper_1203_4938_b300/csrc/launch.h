@@ -83,4 +83,12 @@ bool three_config_available(const ThreeConfig& c);
 cudaError_t three_prepare(const ThreeConfig& c, PersistInfo* info);
 cudaError_t launch_threestep(const ThreeConfig& c, bool inv, const ThreeArgs& a, int grid, cudaStream_t st);
 
+// --- thread-block-cluster single pass (k_cluster.cu) --------------------------
+// N = K * 2^lm (K = 8 or 16 CTAs per transform, DSMEM exchanges).
+bool cluster_config_available(int lm, int k);
+// raise the kernel attributes; *max_clusters = co-resident clusters (0: cannot run)
+cudaError_t cluster_prepare(int lm, int k, int* max_clusters);
+cudaError_t launch_cluster_fft(int lm, int k, bool inv, const float2* in, float2* out, int64_t batch,
+                               const float2* tw, const float2* lo, const float2* hi, int sh, cudaStream_t st);
+
 }  // namespace b300fft

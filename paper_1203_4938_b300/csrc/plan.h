@@ -15,6 +15,7 @@ enum class PlanKind : int {
     FourStep,  // columns + transposed rows, through the workspace
     FourStepPersist,  // both four-step passes in one persistent launch, L2-resident chunks
     ThreeStep,        // three short-transform stages in one persistent launch (N = N1 * M1 * M2)
+    Cluster,          // one transform per thread-block cluster, DSMEM exchanges, one HBM round trip
     TwoD,      // rows pass then in-place columns pass
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
@@ -49,6 +50,7 @@ struct fft_plan_s {
     int64_t pcb = 0;
     int64_t spin_limit = int64_t(1) << 23;
     int withhold_chunk = -1;
+    int cl_lm = 0, cl_k = 0;  // cluster: N = cl_k * 2^cl_lm
     int pG = 0, pnb1g = 0, pnb2g = 0, pD = 1;  // three-stage: groups per chunk, B1 / B2 tiles per group, lookahead
     size_t off_a = 0, off_b = 0, off_c = 0, off_lo = 0, off_hi = 0;  // into d_tables (float2 units)
 

@@ -174,6 +174,12 @@ def test_side_stream_and_graph_capture(torch):
     (18, {"B300FFT_PERSIST_CFG": "9,8,9,8", "B300FFT_CHUNK_MB": "3"}),
     (18, {"B300FFT_PERSIST_CFG": "9,8,9,8", "B300FFT_CHUNK_MB": "64"}),  # one chunk: B tiles wait on A tiles
     (22, {"B300FFT_PERSIST_CFG": "11,4,11,4", "B300FFT_CHUNK_MB": "16"}),
+    # thread-block-cluster single pass (N = K * M on K CTAs, DSMEM exchanges)
+    (15, {"B300FFT_CLUSTER": "1", "B300FFT_CLUSTER_CFG": "12,8"}),
+    (16, {"B300FFT_CLUSTER": "1", "B300FFT_CLUSTER_CFG": "13,8"}),
+    (16, {"B300FFT_CLUSTER": "1", "B300FFT_CLUSTER_CFG": "12,16"}),
+    (17, {"B300FFT_CLUSTER": "1", "B300FFT_CLUSTER_CFG": "14,8"}),
+    (17, {"B300FFT_CLUSTER": "1", "B300FFT_CLUSTER_CFG": "13,16"}),
     # three-stage persistent kernel (N = N1 * M1 * M2)
     (19, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "6,6,7", "B300FFT_CHUNK_MB": "4"}),   # many chunks
     (19, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "6,6,7", "B300FFT_CHUNK_MB": "64"}),  # one chunk
@@ -231,3 +237,24 @@ def test_persistent_wait_timeout_is_reported(torch, monkeypatch, cfg):
         p.check()
         ref = oracle.fft(x.cpu().numpy(), -1)
         assert max_rel_l2(y.cpu().numpy(), ref, -1) <= TOL_FP32
+
+
+@pytest.mark.parametrize("cfg", ["12,8", "13,16"])
+def test_cluster_in_place_and_round_trip(torch, monkeypatch, cfg):
+    """Cluster kernel writing over its own input (every CTA of a cluster loads
+    its chunk before any CTA stores), then the inverse back."""
+    from paper_1203_4938_b300 import fft as F
+    lm, k = (int(v) for v in cfg.split(","))
+    n = k << lm
+    monkeypatch.setenv("B300FFT_CLUSTER", "1")
+    monkeypatch.setenv("B300FFT_CLUSTER_CFG", cfg)
+    x = inputs.uniform_batch(3, n, seed=77)
+    with F.Plan((n,), 3) as p:
+        assert "cluster" in p.describe()
+        d = to_dev(x)
+        p.forward(d, d)
+        torch.cuda.synchronize()
+        assert max_rel_l2(d.cpu().numpy(), oracle.fft(x, -1), -1) <= TOL_FP32
+        p.inverse(d, d)
+        torch.cuda.synchronize()
+        assert max_rel_l2(d.cpu().numpy() / n, x, -1) <= 2 * TOL_FP32
