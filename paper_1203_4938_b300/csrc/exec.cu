@@ -2,6 +2,7 @@
 #include "gplan.h"
 #include "launch.h"
 #include "persist.cuh"
+#include "persist2d.cuh"
 #include "threestep.cuh"
 #include "plan.h"
 
@@ -78,6 +79,31 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch + (int64_t)p->pnch * p->pG), st);
             if (e == cudaSuccess)
                 e = launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2}, inv, a, p->pgrid, st);
+            break;
+        }
+        case PlanKind::TwoDPersist: {
+            if (!want(0)) break;
+            PersistArgs a;
+            a.in = in;
+            a.out = out;
+            a.work = out;
+            a.ctl = static_cast<int*>(p->d_aux);
+            a.status = p->d_status;
+            a.batch = p->batch;
+            a.cb = p->pcb;
+            a.nch = p->pnch;
+            a.na = p->pna;
+            a.nb = p->pnb;
+            a.tw_a = p->d_tables + p->off_a;
+            a.tw_b = p->d_tables + p->off_b;
+            a.lo = nullptr;
+            a.hi = nullptr;
+            a.sh = 0;
+            a.spin_limit = p->spin_limit;
+            a.withhold_chunk = p->withhold_chunk;
+            e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch), st);
+            if (e == cudaSuccess)
+                e = launch_2d_persist(PersistConfig{p->pl1, p->pc, p->pl2, p->ptpc}, inv, a, p->pgrid, st);
             break;
         }
         case PlanKind::Cluster:

@@ -383,7 +383,70 @@ fft_status build_pow2_1d(fft_plan_s* p, int logn) {
     return FFT_OK;
 }
 
+// Persistent 2-D with L2-resident chunks of images (square sizes with a
+// tiling below; images of more than 48 MiB keep the two-launch form).
+// kTwoD[log2 side] = {rows per row tile, columns per column tile, chunk MiB}.
+fft_status build_2d_persist(fft_plan_s* p, int logh, int logw) {
+    static const int kTwoD[12][3] = {{0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {8, 8, 32}, {8, 8, 32}, {4, 4, 32}};
+    if (logh != logw || logw < 9 || logw > 11) return FFT_ERR_UNSUPPORTED;
+    const int64_t hw = int64_t(1) << (logh + logw);
+    if (hw * 8 > (int64_t(48) << 20)) return FFT_ERR_UNSUPPORTED;
+    PersistConfig cfg{logw, kTwoD[logw][0], logh, kTwoD[logw][1]};
+    if (const char* v = std::getenv("B300FFT_2D_CFG")) {
+        int tpc = 0, c = 0;
+        if (std::sscanf(v, "%d,%d", &tpc, &c) == 2) {
+            cfg.c = tpc;
+            cfg.tpc = c;
+        }
+    }
+    if (!persist2d_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+    PersistInfo info;
+    if (persist2d_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t chunk_bytes = int64_t(env_int("B300FFT_CHUNK_MB", kTwoD[logw][2])) << 20;
+    int64_t cb = chunk_bytes / (hw * 8);
+    if (cb < 1) cb = 1;
+    if (cb > p->batch) cb = p->batch;
+    const int64_t nch = (p->batch + cb - 1) / cb;
+    const int64_t na = cb * ((int64_t(1) << logh) / cfg.c), nb = cb * ((int64_t(1) << logw) / cfg.tpc);
+    if (nch * (na + nb) > 0x7fffffffLL) return FFT_ERR_UNSUPPORTED;
+    p->kind = PlanKind::TwoDPersist;
+    p->logn_a = logw;
+    p->logn_b = logh;
+    p->pl1 = cfg.l1;
+    p->pc = cfg.c;
+    p->pl2 = cfg.l2;
+    p->ptpc = cfg.tpc;
+    p->pcb = cb;
+    p->pnch = (int)nch;
+    p->pna = (int)na;
+    p->pnb = (int)nb;
+    const int64_t items = nch * (na + nb), slots = (int64_t)sms * info.blocks_per_sm;
+    p->pgrid = (int)(items < slots ? items : slots);
+    p->spin_limit = env_int("B300FFT_SPIN_LIMIT", 1 << 23);
+    p->withhold_chunk = env_int("B300FFT_DEBUG_WITHHOLD_CHUNK", -1);
+    const size_t ea = (size_t)pow2_table_entries(logw), eb = (size_t)pow2_table_entries(logh);
+    p->off_a = 0;
+    p->off_b = ea;
+    fft_status s = alloc_tables(p, ea + eb);
+    if (s != FFT_OK) return s;
+    if (gen_pow2_table(p->d_tables + p->off_a, logw, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_pow2_table(p->d_tables + p->off_b, logh, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (cudaMalloc(&p->d_aux, sizeof(int) * (size_t)(1 + nch)) != cudaSuccess) return FFT_ERR_ALLOC;
+    p->kernels = 1;
+    std::snprintf(p->desc, sizeof p->desc,
+                  "2d-persist H=2^%d W=2^%d: rows(tpc=%d) then cols(C=%d) threads=%d grid=%d chunk=%lld x %lld", logh,
+                  logw, cfg.c, cfg.tpc, info.threads, p->pgrid, (long long)cb, (long long)nch);
+    return FFT_OK;
+}
+
 fft_status build_pow2_2d(fft_plan_s* p, int logh, int logw) {
+    if (env_int("B300FFT_PERSIST", 1)) {
+        fft_status ps = build_2d_persist(p, logh, logw);
+        if (ps != FFT_ERR_UNSUPPORTED) return ps;
+    }
     if (logw > kRowsMaxLog || logh > kColsMaxLog || logh < 1) return FFT_ERR_UNSUPPORTED;
     p->kind = PlanKind::TwoD;
     p->logn_a = logw;  // rows pass

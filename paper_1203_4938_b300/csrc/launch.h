@@ -73,6 +73,13 @@ cudaError_t persist_prepare(const PersistConfig& c, PersistInfo* info);
 cudaError_t launch_fourstep_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid,
                                     cudaStream_t st);
 
+// --- persistent 2-D (k_2d.cu) --------------------------------------------------
+// PersistConfig fields: l1 = log2 W, c = rows per row tile, l2 = log2 H,
+// tpc = columns per column tile.
+bool persist2d_config_available(const PersistConfig& c);
+cudaError_t persist2d_prepare(const PersistConfig& c, PersistInfo* info);
+cudaError_t launch_2d_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid, cudaStream_t st);
+
 // --- persistent three-stage (k_three.cu) ------------------------------------
 // N = 2^la * 2^lb1 * 2^lb2, each stage length in 2^6 .. 2^8, 4096-point tiles.
 struct ThreeArgs;  // threestep.cuh

@@ -17,6 +17,7 @@ enum class PlanKind : int {
     ThreeStep,        // three short-transform stages in one persistent launch (N = N1 * M1 * M2)
     Cluster,          // one transform per thread-block cluster, DSMEM exchanges, one HBM round trip
     TwoD,      // rows pass then in-place columns pass
+    TwoDPersist,  // both 2-D passes in one persistent launch, L2-resident chunks of images
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
     Ragged,    // persistent work-queue kernel over uneven lengths

@@ -92,7 +92,7 @@ def test_large_batch_tiny_n(torch):
 
 # ---------------------------------------------------------------- 2-D
 @pytest.mark.parametrize("h,w,b", [(2, 2, 1), (16, 64, 3), (64, 16, 2), (256, 512, 2), (1024, 1024, 1),
-                                   (4096, 64, 1), (32, 8192, 1)])
+                                   (4096, 64, 1), (32, 8192, 1), (512, 512, 5), (2048, 2048, 2)])
 def test_2d(torch, h, w, b):
     rng = np.random.default_rng(h * 7 + w)
     x = inputs.image_batch(rng, b, h, w)
@@ -258,3 +258,29 @@ def test_cluster_in_place_and_round_trip(torch, monkeypatch, cfg):
         p.inverse(d, d)
         torch.cuda.synchronize()
         assert max_rel_l2(d.cpu().numpy() / n, x, -1) <= 2 * TOL_FP32
+
+
+@pytest.mark.parametrize("side,b,env", [
+    (512, 7, {"B300FFT_CHUNK_MB": "1"}),                    # one image per chunk, ragged tail
+    (1024, 3, {"B300FFT_2D_CFG": "16,16"}),
+    (2048, 3, {"B300FFT_2D_CFG": "4,4", "B300FFT_CHUNK_MB": "64"}),  # one chunk
+    (2048, 2, {"B300FFT_PERSIST": "0"}),                    # two-launch form
+])
+def test_2d_persistent_variants(torch, monkeypatch, side, b, env):
+    from paper_1203_4938_b300 import fft as F
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    x = inputs.image_batch(np.random.default_rng(side + b), b, side, side)
+    with F.Plan((side, side), b) as p:
+        want = "2d H=" if env.get("B300FFT_PERSIST") == "0" else "2d-persist"
+        assert want in p.describe(), p.describe()
+    for d in (-1, +1):
+        y = run((side, side), b, x, d)
+        ref = oracle.fft2(x, d)
+        assert max_rel_l2(y.reshape(b, -1), ref.reshape(b, -1), -1) <= TOL_FP32, (side, env, d)
+
+
+def test_2d_in_place(torch):
+    x = inputs.image_batch(np.random.default_rng(11), 2, 1024, 1024)
+    y = run((1024, 1024), 2, x, -1, inplace=True)
+    assert max_rel_l2(y.reshape(2, -1), oracle.fft2(x, -1).reshape(2, -1), -1) <= TOL_FP32
