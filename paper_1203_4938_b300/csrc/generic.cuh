@@ -55,6 +55,7 @@ struct GStage {
     int inv;            // direction of this stage's transform
     int pre, post;
     int sh;
+    int tmpl;  // > 0: power-of-two four-step stage run by the templated tiles: 2 * log2 N + (0: A, 1: B)
     int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
     int64_t pre_tab, post_tab;             // table offsets in the pool
@@ -236,6 +237,48 @@ __device__ __forceinline__ float2* g_buf_out(const GExecArgs& a, const GTransfor
     }
 }
 
+// Power-of-two four-step stage of a transform of N = 2^L1 * 2^L2 with the
+// register-staged templated tiles of the batched path (256 threads):
+// A = C columns with the W_N twiddle into the transform's work buffer,
+// B = TPC rows with the transposed store.  Tables: pre_tab = Stockham table
+// of 2^L1, post_tab = of 2^L2, lo / hi / sh = two-level W_N table.
+template <int L1, int C, int L2, int TPC>
+__device__ __forceinline__ void g_fourstep_tile(const GExecArgs& a, const GTransform& x, const GStage& st, int tile,
+                                                float2* smem) {
+    static_assert(ColsCfg<L1, C>::THREADS == kGThreads && RowsTCfg<L2, TPC>::THREADS == kGThreads,
+                  "templated stages run on the executor's 256 threads");
+    constexpr int64_t N1 = int64_t(1) << L1, N2 = int64_t(1) << L2;
+    const uint64_t pol = l2_policy_evict_last();
+    if (st.tmpl & 1) {
+        const float2* src = a.work + x.w1_off + (int64_t)tile * TPC * N2;
+        float2* dst = a.out + x.out_off + (int64_t)tile * TPC;
+        if (st.inv) rowsT_tile<L2, TPC, true, Ld::Cg, St::Stream>(src, dst, N1, a.pool + st.post_tab, smem, pol);
+        else rowsT_tile<L2, TPC, false, Ld::Cg, St::Stream>(src, dst, N1, a.pool + st.post_tab, smem, pol);
+    } else {
+        const int64_t c0 = (int64_t)tile * C;
+        const float2* src = a.in + x.in_off + c0;
+        float2* dst = a.work + x.w1_off + c0;
+        const float2 *lo = a.pool + st.lo, *hi = a.pool + st.hi;
+        if (st.inv)
+            cols_tile<L1, C, true, true, Ld::Stream, St::Keep>(src, dst, N2, (uint32_t)c0, a.pool + st.pre_tab, lo, hi,
+                                                               st.sh, smem, pol);
+        else
+            cols_tile<L1, C, false, true, Ld::Stream, St::Keep>(src, dst, N2, (uint32_t)c0, a.pool + st.pre_tab, lo,
+                                                                hi, st.sh, smem, pol);
+    }
+}
+
+__device__ __forceinline__ void g_pow2_tile(const GExecArgs& a, const GTransform& x, const GStage& st, int tile,
+                                            float2* smem) {
+    switch (st.tmpl >> 1) {
+        case 13: g_fourstep_tile<6, 64, 7, 32>(a, x, st, tile, smem); break;
+        case 14: g_fourstep_tile<7, 32, 7, 32>(a, x, st, tile, smem); break;
+        case 15: g_fourstep_tile<7, 32, 8, 16>(a, x, st, tile, smem); break;
+        case 16: g_fourstep_tile<8, 16, 8, 16>(a, x, st, tile, smem); break;
+        default: break;
+    }
+}
+
 // Run queue item p (tile of one stage of one transform).
 __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* smem, int* s_ok) {
     const uint64_t it = a.items[p];
@@ -263,12 +306,16 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
         __syncthreads();
         if (!*s_ok) return;
     }
-    const int line0 = tile * st.lpt;
-    const int nl = min(st.lpt, st.nlines - line0);
-    const float2* gin = g_buf_in(a, x, st.in_buf);
-    float2* gout = g_buf_out(a, x, st.out_buf);
-    if (st.inv) g_tile_dir<true>(st, sh, a.pool, gin, gout, line0, nl, smem, a.line_off);
-    else g_tile_dir<false>(st, sh, a.pool, gin, gout, line0, nl, smem, a.line_off);
+    if (st.tmpl) {
+        g_pow2_tile(a, x, st, tile, smem);
+    } else {
+        const int line0 = tile * st.lpt;
+        const int nl = min(st.lpt, st.nlines - line0);
+        const float2* gin = g_buf_in(a, x, st.in_buf);
+        float2* gout = g_buf_out(a, x, st.out_buf);
+        if (st.inv) g_tile_dir<true>(st, sh, a.pool, gin, gout, line0, nl, smem, a.line_off);
+        else g_tile_dir<false>(st, sh, a.pool, gin, gout, line0, nl, smem, a.line_off);
+    }
     if (s + 1 < x.nstages && !a.single) {
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -83,6 +83,15 @@ struct Builder {
     std::vector<PassTab> pass_tabs;
     std::vector<RootTab> root_tabs;
     std::vector<BlueTab> blue_list;
+    std::map<int, int64_t> pow2_tabs;  // log2 L -> offset of the templated tiles' Stockham table
+
+    int64_t pow2_table(int logn) {
+        auto it = pow2_tabs.find(logn);
+        if (it != pow2_tabs.end()) return it->second;
+        const int64_t o = alloc(pow2_table_entries(logn));
+        pow2_tabs[logn] = o;
+        return o;
+    }
 
     int64_t alloc(int64_t n) {
         int64_t o = pool_size;
@@ -133,6 +142,11 @@ struct Builder {
         return t;
     }
 };
+
+// Power-of-two lengths the stage graph runs with the templated tiles.
+bool pow2_templated(int64_t n) {
+    return n >= (int64_t(1) << 13) && n <= (int64_t(1) << 16) && (n & (n - 1)) == 0 && env_i("B300FFT_G_POW2T", 1) != 0;
+}
 
 GStage base_stage(int shape, int nlines, int lpt, int inv) {
     GStage s{};
@@ -199,6 +213,38 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
             }
             (d ? i : f).push_back(s);
         }
+    } else if (pow2_templated(n)) {
+        // 2^13 .. 2^16: the batched path's register-staged tiles, (log2 N1, C, log2 N2, TPC) as below
+        int lg = 0;
+        while ((int64_t(1) << lg) < n) ++lg;
+        static const int kT[17][4] = {{0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
+                                      {6, 64, 7, 32}, {7, 32, 7, 32}, {7, 32, 8, 16}, {8, 16, 8, 16}};
+        const int l1 = kT[lg][0], c = kT[lg][1], l2 = kT[lg][2], tpc = kT[lg][3];
+        const int sa = B.shape(1 << l1);
+        if (sa < 0) return false;
+        int shs;
+        auto tabs = B.tw4(n, &shs);
+        const int64_t ta = B.pow2_table(l1), tb = B.pow2_table(l2);
+        for (int d = 0; d < 2; ++d) {
+            GStage a = base_stage(sa, 1, 1, d);
+            a.ntiles = (1 << l2) / c;
+            a.tmpl = 2 * lg;
+            a.in_buf = G_BUF_IN;
+            a.out_buf = G_BUF_W1;
+            a.pre_tab = ta;
+            a.lo = tabs.first;
+            a.hi = tabs.second;
+            a.sh = shs;
+            GStage b = base_stage(sa, 1, 1, d);
+            b.ntiles = (1 << l1) / tpc;
+            b.tmpl = 2 * lg + 1;
+            b.in_buf = G_BUF_W1;
+            b.out_buf = G_BUF_OUT;
+            b.post_tab = tb;
+            (d ? i : f).push_back(a);
+            (d ? i : f).push_back(b);
+        }
+        *w1 = n;
     } else if (is_smooth(n)) {
         int64_t n1, n2;
         if (!split_four(n, cfg.tile_max, cfg.split_n2, &n1, &n2)) return false;
@@ -338,7 +384,7 @@ GExecArgs make_args(const GraphPlan* gp, const float2* in, float2* out, bool inv
     a.shapes = gp->shapes;
     a.stages = gp->stages[inv ? 1 : 0];
     a.xf = gp->xf;
-    a.items = gp->items;
+    a.items = single ? gp->items : gp->items_lag;
     a.nitems = gp->nitems;
     a.ctl = gp->ctl;
     a.status = d_status;
@@ -621,6 +667,44 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
     }
     if (items.size() >= (size_t)0x7fffffff) return FFT_ERR_UNSUPPORTED;
 
+    // Persistent-launch order: transforms in the same (largest kind first)
+    // order, stage s of a transform placed `lag` items after its stage s-1,
+    // so each intermediate is read back soon (from L2) while every
+    // dependency still precedes its consumers in the queue.
+    std::vector<uint64_t> items_lag;
+    {
+        int dev0 = 0, sms0 = 148;
+        cudaGetDevice(&dev0);
+        cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
+        const int64_t lag = env_i("B300FFT_G_LAG", 2 * 3 * sms0);
+        struct Grp {
+            int64_t key;
+            int s, t, ntiles;
+        };
+        std::vector<Grp> grps;
+        int64_t k0 = 0;
+        for (size_t ki = 0; ki < uniq.size(); ++ki) {
+            const Kind& k = kinds[uniq[ki]];
+            for (int t : by_kind[ki]) {
+                int64_t key = k0;
+                for (int s2 = 0; s2 < k.nstages; ++s2) {
+                    const int nt = B.st_f[k.first + s2].ntiles;
+                    grps.push_back({key, s2, t, nt});
+                    if (s2 == 0) k0 += nt;
+                    key += std::max<int64_t>(lag, nt);
+                }
+            }
+        }
+        std::stable_sort(grps.begin(), grps.end(), [](const Grp& x, const Grp& y) {
+            return x.key != y.key ? x.key < y.key : x.s < y.s;
+        });
+        items_lag.reserve(items.size());
+        for (const Grp& g : grps)
+            for (int tile = 0; tile < g.ntiles; ++tile)
+                items_lag.push_back(((uint64_t)g.t << 32) | ((uint64_t)g.s << 24) | (uint64_t)tile);
+        if (items_lag.size() != items.size()) return FFT_ERR_UNSUPPORTED;
+    }
+
     // device data
     cudaStream_t st = 0;
     if (cudaMalloc(&gp->pool, sizeof(float2) * (size_t)std::max<int64_t>(B.pool_size, 2)) != cudaSuccess)
@@ -629,6 +713,8 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
         if (gen_pass_table(gp->pool + t.off, t.ns, t.r, st) != cudaSuccess) return FFT_ERR_CUDA;
     for (auto& t : B.root_tabs)
         if (gen_root_table(gp->pool + t.off, t.count, t.mult, t.n, st) != cudaSuccess) return FFT_ERR_CUDA;
+    for (auto& t : B.pow2_tabs)
+        if (gen_pow2_table(gp->pool + t.second, t.first, st) != cudaSuccess) return FFT_ERR_CUDA;
     if (!B.blue_list.empty()) {
         int64_t maxM = 0;
         for (auto& b : B.blue_list) maxM = std::max(maxM, b.M);
@@ -649,6 +735,7 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
     if (upload(&gp->stages[1], B.st_i) != cudaSuccess) return FFT_ERR_ALLOC;
     if (upload(&gp->xf, xf) != cudaSuccess) return FFT_ERR_ALLOC;
     if (upload(&gp->items, items) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (upload(&gp->items_lag, items_lag) != cudaSuccess) return FFT_ERR_ALLOC;
     if (upload(&gp->line_off, line_off) != cudaSuccess) return FFT_ERR_ALLOC;
     gp->nitems = (int)items.size();
     gp->ncounters = ctr;
@@ -691,12 +778,14 @@ void graph_plan_free(GraphPlan* gp) {
     cudaFree(gp->shapes);
     cudaFree(gp->xf);
     cudaFree(gp->items);
+    cudaFree(gp->items_lag);
     cudaFree(gp->ctl);
     cudaFree(gp->work);
     gp->pool = nullptr;
     gp->shapes = nullptr;
     gp->xf = nullptr;
     gp->items = nullptr;
+    gp->items_lag = nullptr;
     gp->ctl = nullptr;
     gp->work = nullptr;
 }

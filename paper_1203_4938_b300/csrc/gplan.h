@@ -29,7 +29,8 @@ struct GraphPlan {
     GShape* shapes = nullptr;
     GStage* stages[2] = {nullptr, nullptr};  // forward, inverse
     GTransform* xf = nullptr;
-    uint64_t* items = nullptr;
+    uint64_t* items = nullptr;      // queue in stage rounds (per-stage launch groups)
+    uint64_t* items_lag = nullptr;  // queue of the persistent launch (stages lagged per transform)
     int* ctl = nullptr;
     float2* work = nullptr;
     size_t work_bytes = 0;

@@ -100,6 +100,21 @@ def test_ragged_small_mix(torch, per_size):
         assert _ragged_check(torch, lengths, data, per_size, d) <= TOL_FP32
 
 
+@pytest.mark.parametrize("env", [{}, {"B300FFT_G_POW2T": "0"}, {"B300FFT_G_LAG": "1"}, {"B300FFT_G_LAG": "100000"}])
+def test_ragged_pow2_templated_stages(torch, monkeypatch, env):
+    """Power-of-two lengths 2^13..2^16 inside a ragged batch run as templated
+    four-step stages (or, with B300FFT_G_POW2T=0, as runtime-radix stages);
+    the persistent queue lags each transform's second stage (B300FFT_G_LAG
+    items, 1 = right behind).  Every transform is compared in full."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    lengths = [8192, 16384, 32768, 65536, 3 * 2 ** 13, 8192, 65536, 100, 4096, 16384, 2 ** 13, 7 * 2 ** 12]
+    data = np.random.default_rng(21).standard_normal(2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    for per_size in (False, True):
+        for d in (-1, +1):
+            assert _ragged_check(torch, lengths, data, per_size, d, full_limit=70000) <= TOL_FP32, (env, per_size, d)
+
+
 def test_ragged_edge_lengths(torch):
     lengths = [1, 2, 3, 4096, 4097, 17, 65536, 64, 5, 7 * 2 ** 13, 1, 2053]
     data = np.random.default_rng(5).standard_normal(2 * sum(lengths)).astype(np.float32).view(np.complex64)
