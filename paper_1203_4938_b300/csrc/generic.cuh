@@ -91,35 +91,76 @@ struct GExecArgs {
 
 __device__ __forceinline__ int gpad(int a) { return a + (a >> 4); }
 
+// Division by a runtime divisor d (1 <= d < 2^16) of numerators e < 2^16 as
+// one multiply-high: q = floor(e * ceil(2^32 / d) / 2^32), exact whenever
+// e * d < 2^32 (the rounding error of the reciprocal stays below 1/d).
+struct FastDiv {
+    uint32_t d, m;
+    __device__ __forceinline__ explicit FastDiv(uint32_t dd)
+        : d(dd), m(dd > 1 ? (uint32_t)((0x100000000ull + dd - 1) / dd) : 0u) {}
+    __device__ __forceinline__ uint32_t div(uint32_t e) const { return d > 1 ? __umulhi(e, m) : e; }
+    __device__ __forceinline__ uint32_t mod(uint32_t e) const { return e - div(e) * d; }
+};
+
 // Pass p of a tile: every radix-R butterfly of nl lines.  Intermediate passes
 // go src -> dst in shared memory; the last pass stores to global memory.
 template <int R, bool INV>
 __device__ __forceinline__ void g_pass(const GStage& st, const GShape& sh, int p, const float2* __restrict__ pool,
                                        const float2* src, float2* dst, int Lp, int line0, int nl, bool last,
-                                       float2* __restrict__ gout, const int64_t* __restrict__ line_off) {
+                                       float2* __restrict__ gout, const int64_t* s_loff) {
     const int L = sh.L;
     const int Ns = sh.ns[p];
     const int stride = L / R;  // butterflies per line
     const int nbf = nl * stride;
     const float2* tw = pool + sh.tw[p];
     const bool lf = last && st.out_line_fast;
+    const FastDiv by_nl((uint32_t)nl), by_stride((uint32_t)stride), by_ns((uint32_t)Ns);
     for (int bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
         int line, b;
         if (lf) {
-            line = bf % nl;
-            b = bf / nl;
+            b = (int)by_nl.div((uint32_t)bf);
+            line = bf - b * nl;
         } else {
-            line = bf / stride;
+            line = (int)by_stride.div((uint32_t)bf);
             b = bf - line * stride;
         }
         const float2* s = src + line * Lp;
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[gpad(b + r * stride)];
-        const int k = b % Ns;
+        const int k = (int)by_ns.mod((uint32_t)b);
         if (p > 0) {
+            const float2* tp = tw + k;  // block [(r-1)*Ns + k] = W_{Ns R}^{k r}
+            if constexpr (R == 16) {
+                // six loads; the other nine twiddles are one product of two loaded ones
+                float2 w[16];
+                w[1] = __ldg(tp);
+                w[2] = __ldg(tp + Ns);
+                w[3] = __ldg(tp + 2 * Ns);
+                w[4] = __ldg(tp + 3 * Ns);
+                w[8] = __ldg(tp + 7 * Ns);
+                w[12] = __ldg(tp + 11 * Ns);
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = twmul<INV>(v[r], __ldg(tw + (r - 1) * Ns + k));
+                for (int h = 4; h <= 12; h += 4)
+#pragma unroll
+                    for (int l = 1; l <= 3; ++l) w[h + l] = cmul(w[h], w[l]);
+#pragma unroll
+                for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], w[r]);
+            } else if constexpr (R == 8) {
+                float2 w[8];
+                w[1] = __ldg(tp);
+                w[2] = __ldg(tp + Ns);
+                w[4] = __ldg(tp + 3 * Ns);
+                w[3] = cmul(w[1], w[2]);
+                w[5] = cmul(w[1], w[4]);
+                w[6] = cmul(w[2], w[4]);
+                w[7] = cmul(w[3], w[4]);
+#pragma unroll
+                for (int r = 1; r < 8; ++r) v[r] = twmul<INV>(v[r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = twmul<INV>(v[r], __ldg(tp + (r - 1) * Ns));
+            }
         }
         dft<R, 0, 1, INV>(v);
         if (!last) {
@@ -130,8 +171,7 @@ __device__ __forceinline__ void g_pass(const GStage& st, const GShape& sh, int p
         } else {
             // natural order: output element k = b + r*stride of line line0+line
             const int aline = line0 + line;
-            const int64_t lo_line =
-                st.line_tab >= 0 ? __ldg(line_off + st.line_tab + aline) : (int64_t)aline * st.out_ls;
+            const int64_t lo_line = st.line_tab >= 0 ? s_loff[line] : (int64_t)aline * st.out_ls;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int kk = b + r * stride;
@@ -161,9 +201,16 @@ __device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __r
     const int Lp = gpad(L) + 1;
     float2* bufA = smem;
     float2* bufB = smem + kGBuf;
+    // element offsets of the tile's lines when they are separate transforms
+    __shared__ int64_t s_loff[kGMaxLines];
+    if (st.line_tab >= 0) {
+        for (int l = threadIdx.x; l < nl; l += kGThreads) s_loff[l] = __ldg(line_off + st.line_tab + line0 + l);
+        __syncthreads();
+    }
     // 1. load (coalesced), pre-multiply, zero beyond in_valid; U loads in
     // flight per thread before their shared-memory stores
     const int tot = nl * L;
+    const FastDiv by_nl((uint32_t)nl), by_L((uint32_t)L);
     constexpr int U = 4;
     for (int e0 = threadIdx.x; e0 < tot; e0 += U * kGThreads) {
         float2 v[U];
@@ -176,14 +223,13 @@ __device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __r
             if (e < tot) {
                 int line, i;
                 if (st.in_line_fast) {
-                    line = e % nl;
-                    i = e / nl;
+                    i = (int)by_nl.div((uint32_t)e);
+                    line = e - i * nl;
                 } else {
-                    line = e / L;
+                    line = (int)by_L.div((uint32_t)e);
                     i = e - line * L;
                 }
-                const int64_t lb = st.line_tab >= 0 ? __ldg(line_off + st.line_tab + line0 + line)
-                                                    : (int64_t)(line0 + line) * st.in_ls;
+                const int64_t lb = st.line_tab >= 0 ? s_loff[line] : (int64_t)(line0 + line) * st.in_ls;
                 const int64_t off = lb + (int64_t)i * st.in_es;
                 dst[u] = line * Lp + gpad(i);
                 if (off < st.in_valid) {
@@ -206,7 +252,7 @@ __device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __r
         switch (sh.radix[p]) {
 #define B300_G(RR)                                                                    \
     case RR:                                                                          \
-        g_pass<RR, INV>(st, sh, p, pool, src, dst, Lp, line0, nl, last, gout, line_off); \
+        g_pass<RR, INV>(st, sh, p, pool, src, dst, Lp, line0, nl, last, gout, s_loff);   \
         break;
             B300_G(1) B300_G(2) B300_G(3) B300_G(4) B300_G(5) B300_G(7) B300_G(8) B300_G(16)
 #undef B300_G
