@@ -55,7 +55,8 @@ struct GStage {
     int inv;            // direction of this stage's transform
     int pre, post;
     int sh;
-    int tmpl;  // > 0: power-of-two four-step stage run by the templated tiles: 2 * log2 N + (0: A, 1: B)
+    int tmpl;  // > 0: templated tiles: 2 * log2 N + (0: A, 1: B) of a power-of-two four-step,
+               // or 100 + log2 N2: second stage (rows of 2^L2) of a mixed-length four-step
     int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
     int64_t pre_tab, post_tab;             // table offsets in the pool
@@ -314,8 +315,30 @@ __device__ __forceinline__ void g_fourstep_tile(const GExecArgs& a, const GTrans
     }
 }
 
+// Second stage of a mixed-length four-step (N = N1 * 2^L2, N1 = nlines not a
+// power of two): TPC rows of 2^L2 with the transposed store, templated.
+template <int L2, int TPC>
+__device__ __forceinline__ void g_rowsT_stage(const GExecArgs& a, const GTransform& x, const GStage& st, int tile,
+                                              float2* smem) {
+    static_assert(RowsTCfg<L2, TPC>::THREADS == kGThreads, "256 threads");
+    constexpr int64_t N2 = int64_t(1) << L2;
+    const uint64_t pol = l2_policy_evict_last();
+    const float2* src = a.work + x.w1_off + (int64_t)tile * TPC * N2;
+    float2* dst = a.out + x.out_off + (int64_t)tile * TPC;
+    if (st.inv) rowsT_tile<L2, TPC, true, Ld::Cg, St::Stream>(src, dst, (int64_t)st.nlines, a.pool + st.post_tab, smem, pol);
+    else rowsT_tile<L2, TPC, false, Ld::Cg, St::Stream>(src, dst, (int64_t)st.nlines, a.pool + st.post_tab, smem, pol);
+}
+
 __device__ __forceinline__ void g_pow2_tile(const GExecArgs& a, const GTransform& x, const GStage& st, int tile,
                                             float2* smem) {
+    if (st.tmpl >= 100) {  // 100 + L2: mixed four-step second stage
+        switch (st.tmpl - 100) {
+            case 7: g_rowsT_stage<7, 32>(a, x, st, tile, smem); break;
+            case 8: g_rowsT_stage<8, 16>(a, x, st, tile, smem); break;
+            default: break;
+        }
+        return;
+    }
     switch (st.tmpl >> 1) {
         case 13: g_fourstep_tile<6, 64, 7, 32>(a, x, st, tile, smem); break;
         case 14: g_fourstep_tile<7, 32, 7, 32>(a, x, st, tile, smem); break;

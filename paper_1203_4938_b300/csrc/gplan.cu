@@ -273,6 +273,14 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
             b.out_ls = 1;
             b.out_es = n1;
             b.in_valid = b.out_valid = n;
+            // rows of 128 or 256 points and a line count the rows-per-tile divide:
+            // the templated transposed-row tile (32 or 16 rows, 256 threads)
+            const int tpc2 = n2 == 128 ? 32 : (n2 == 256 ? 16 : 0);
+            if (tpc2 && n1 % tpc2 == 0 && env_i("B300FFT_G_POW2T", 1) != 0) {
+                b.tmpl = 100 + (n2 == 128 ? 7 : 8);
+                b.ntiles = (int)(n1 / tpc2);
+                b.post_tab = B.pow2_table(n2 == 128 ? 7 : 8);
+            }
             (d ? i : f).push_back(a);
             (d ? i : f).push_back(b);
         }
