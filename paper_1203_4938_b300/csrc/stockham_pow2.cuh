@@ -192,8 +192,12 @@ __device__ __forceinline__ void xsync() {
     else __syncthreads();
 }
 
-// All passes from P on (CS interleaved columns in the exchange buffer).
-template <class PL, int P, bool INV, bool WARP_ONLY, int CS>
+// All passes from P on (CS interleaved columns in the exchange buffer).  With
+// LAST_SYNC = false the barrier after the last gather is left out: the caller
+// then rewrites the exchange area only after a barrier of its own (tile loop,
+// CTA exit, cluster barrier).  Measured: faster for the column tiles of the
+// persistent kernels, slower for the single-pass rows kernel.
+template <class PL, int P, bool INV, bool WARP_ONLY, int CS, bool LAST_SYNC = true>
 __device__ __forceinline__ void run_passes(float2 (&v)[PL::R], int t, float2* s, int coff,
                                            const float2* __restrict__ tw) {
     pass_compute<PL, P, INV>(v, t, tw);
@@ -201,8 +205,8 @@ __device__ __forceinline__ void run_passes(float2 (&v)[PL::R], int t, float2* s,
         pass_scatter<PL, P, CS>(v, t, s, coff);
         xsync<WARP_ONLY>();
         pass_gather<PL, CS>(v, t, s, coff);
-        xsync<WARP_ONLY>();
-        run_passes<PL, P + 1, INV, WARP_ONLY, CS>(v, t, s, coff, tw);
+        if constexpr (LAST_SYNC || P + 2 < PL::NPASS) xsync<WARP_ONLY>();
+        run_passes<PL, P + 1, INV, WARP_ONLY, CS, LAST_SYNC>(v, t, s, coff, tw);
     }
 }
 
@@ -356,7 +360,7 @@ __device__ __forceinline__ void cols_tile_regs(float2 (&v)[P2Plan<LOGN>::R], flo
         if constexpr (PL::NPASS == 1) __syncthreads();
     }
 
-    run_passes<PL, 0, INV, false, C>(v, t, smem, c, tw);
+    run_passes<PL, 0, INV, false, C, false>(v, t, smem, c, tw);
 
     if constexpr (TW) {
         const float2 w0 = root2(tw_lo, tw_hi, (col0 + (uint32_t)c) * tws * (uint32_t)t, sh);
