@@ -41,11 +41,10 @@ METRIC = "C2C FFT GFLOP/s (5N*log2N/t), fwd+inv sweep N=2^10..2^24, 2^26 complex
 # --no-cpu` (mean of the forward and inverse launches).  The numbers belong to
 # the kernel sources hashed in TRAFFIC_SOURCES; when those files change the
 # benchmark reports the traffic as null until a new capture replaces them.
-MEASURED_DRAM_MB = {10: 1017, 11: 1020, 12: 1020, 13: 1022, 14: 1022, 15: 1343, 16: 1018, 17: 1421, 18: 1456,
-                    19: 1023, 20: 1122, 21: 2150, 22: 2151, 23: 2018, 24: 2168}
+MEASURED_DRAM_MB = {10: 1018, 11: 1020, 12: 1020, 13: 1022, 14: 1022, 15: 1356, 16: 1018, 17: 1422, 18: 1457, 19: 1023, 20: 1131, 21: 2152, 22: 2152, 23: 2018, 24: 2171}
 TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threestep.cuh", "kernels_launch.cuh",
                    "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu", "fft_api.cu", "exec.cu"]
-TRAFFIC_SOURCES_SHA = "c852a6ca3d0c4241"
+TRAFFIC_SOURCES_SHA = "3eec3f8a2882f52b"
 
 
 def traffic_sources_sha() -> str:
