@@ -131,10 +131,10 @@ __device__ __forceinline__ int three_wait(const ThreeArgs& a, const int* dep, in
     return 1;
 }
 
-// One CTA per queue item at a time, with the bookkeeping of
-// k_fourstep_persist: the next item is dequeued at the tile start, a B tile
-// waits (bounded) for its producers before loading, and a producing tile
-// signals right after its stores.
+// One CTA per queue item at a time: the next item is dequeued at the tile
+// start, a B tile waits (bounded) for its producers before loading, and a
+// producing tile is signalled (and a B2 tile's input lines dropped) right
+// after the next loop barrier -- before this CTA can wait on anything.
 template <int LA, int LB1, int LB2, bool INV>
 __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
     using CF = ThreeCfg<LA, LB1, LB2>;
@@ -148,9 +148,21 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
     __shared__ int s_item[2], s_ok;
     const uint64_t pol = l2_policy_evict_last();
     const int total = a.nch * (a.na + a.nb);
+    int* pend = nullptr;         // thread 0: counter of the previous tile, signalled after the loop barrier
+    const char* drop = nullptr;  // first input row of the previous B2 tile, dropped after the loop barrier
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl, 1);
     for (int it = 0;; it ^= 1) {
-        __syncthreads();
+        __syncthreads();  // the previous tile's stores and reads are done
+        if (threadIdx.x == 0 && pend) {  // release: before any wait of this CTA
+            __threadfence();
+            atomicAdd(pend, 1);
+            pend = nullptr;
+        }
+        if (drop) {
+            for (int l = threadIdx.x; l < TPC * CF::RUN_LINES; l += CF::THREADS)
+                l2_discard_line(drop + (int64_t)(l / CF::RUN_LINES) * N2 * 8 + (int64_t)(l % CF::RUN_LINES) * 128);
+            drop = nullptr;
+        }
         const int p = s_item[it];
         if (p >= total) break;
         if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.ctl, 1);
@@ -168,11 +180,7 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
                 cols_tile_regs<LA, CA, INV, true, St::Keep>(v, a.work + tr * N + col0, N2, col0, a.tw_a, a.lo, a.hi,
                                                             a.sh, smem, pol);
             }
-            __syncthreads();
-            if (threadIdx.x == 0 && c != a.withhold_chunk) {
-                __threadfence();
-                atomicAdd(a.ctl + 1 + c, 1);
-            }
+            if (threadIdx.x == 0 && c != a.withhold_chunk) pend = a.ctl + 1 + c;
             continue;
         }
         if (threadIdx.x == 0) {
@@ -197,11 +205,7 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
                 cols_tile_regs<LB1, CB, INV, true, St::Keep>(v, base, M2, col0, a.tw_b1, a.lo, a.hi, a.sh, smem, pol,
                                                              (uint32_t)N1);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(a.ctl + 1 + a.nch + c * a.G + g, 1);
-            }
+            if (threadIdx.x == 0) pend = a.ctl + 1 + a.nch + c * a.G + g;
         } else if (ok && tr < a.batch) {
             const float2* base = a.work + tr * N + k10 * N2 + (int64_t)r * M2;
             const float2* src = base + (int64_t)(threadIdx.x / TC) * N2 + (threadIdx.x & (TC - 1));
@@ -209,10 +213,7 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = __ldcg(src + i * TC);
             rowsT_tile_regs<LB2, TPC, INV, St::Stream>(v, a.out + tr * N + k10 + N1 * r, N1 * M1, a.tw_b2, smem, pol);
-            __syncthreads();  // the tile's input rows are consumed: drop them from L2
-            const char* drop = reinterpret_cast<const char*>(base);
-            for (int l = threadIdx.x; l < TPC * CF::RUN_LINES; l += CF::THREADS)
-                l2_discard_line(drop + (int64_t)(l / CF::RUN_LINES) * N2 * 8 + (int64_t)(l % CF::RUN_LINES) * 128);
+            drop = reinterpret_cast<const char*>(base);
         }
     }
 }
