@@ -50,10 +50,26 @@ __global__ void __launch_bounds__(kImgThreads) k_image_steps(const uint8_t* __re
     const int64_t h2 = h / 2, w2 = w / 2;
     float* cbo = CB + img * h2 * w2;
     float* cro = CR + img * h2 * w2;
-    // steps 1 and 2 on the tile's quads
-    constexpr int QW = kImgTW / 2, NQ = (kImgTH / 2) * QW;
+    // steps 1 and 2 on the tile's quads: every load of the thread's quads is
+    // issued first (24 16-bit loads in flight), then the arithmetic
+    constexpr int QW = kImgTW / 2, NQ = (kImgTH / 2) * QW, KQ = NQ / kImgThreads;
+    uint32_t raw[KQ][6];
 #pragma unroll
-    for (int k = 0; k < NQ / kImgThreads; ++k) {
+    for (int k = 0; k < KQ; ++k) {
+        const int qd = threadIdx.x + k * kImgThreads;
+        const int qy = qd / QW, qx = qd - qy * QW;
+        const int64_t gy = y0 + 2 * qy, gx = x0 + 2 * qx;
+        const bool in = gy < h && gx < w;
+#pragma unroll
+        for (int row = 0; row < 2; ++row) {
+            // 6 bytes R G B R G B at an even byte offset: three 16-bit loads
+            const uint16_t* p = reinterpret_cast<const uint16_t*>(src + ((gy + row) * w + gx) * 3);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) raw[k][3 * row + q] = in ? (uint32_t)__ldg(p + q) : 0u;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KQ; ++k) {
         const int qd = threadIdx.x + k * kImgThreads;
         const int qy = qd / QW, qx = qd - qy * QW;
         const int64_t gy = y0 + 2 * qy, gx = x0 + 2 * qx;
@@ -61,9 +77,7 @@ __global__ void __launch_bounds__(kImgThreads) k_image_steps(const uint8_t* __re
         float r[4], g[4], b[4];
 #pragma unroll
         for (int row = 0; row < 2; ++row) {
-            // 6 bytes R G B R G B at an even byte offset: three 16-bit loads
-            const uint16_t* p = reinterpret_cast<const uint16_t*>(src + ((gy + row) * w + gx) * 3);
-            const uint32_t a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2);
+            const uint32_t a0 = raw[k][3 * row], a1 = raw[k][3 * row + 1], a2 = raw[k][3 * row + 2];
             r[2 * row] = (float)(a0 & 255u);
             g[2 * row] = (float)(a0 >> 8);
             b[2 * row] = (float)(a1 & 255u);
