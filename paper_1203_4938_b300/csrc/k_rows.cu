@@ -5,8 +5,8 @@ namespace b300fft {
 
 #define B300_PLAIN_CASES(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14)
 
-int rows_tpc(int logn) { return rows_default_tpc(logn); }
-int rows_threads(int logn) { return (logn >= 4 ? (1 << logn) / 16 : 1) * rows_default_tpc(logn); }
+int rows_tpc(int logn) { return rows_tpc_rt(logn); }
+int rows_threads(int logn) { return (logn >= 4 ? (1 << logn) / rows_rt(logn) : 1) * rows_tpc_rt(logn); }
 
 cudaError_t rows_prepare(int logn) {
     switch (logn) {

@@ -16,29 +16,38 @@ inline cudaError_t grid_of(int64_t units, int per, unsigned* g) {
 }
 
 // ---- plain rows --------------------------------------------------------
-constexpr int rows_default_tpc(int logn) {
-    const int t = logn >= 4 ? (1 << logn) / 16 : 1;
+// Lengths (bit mask of log2 N) whose rows kernel holds 32 elements per thread
+// (two radix-16 butterflies per pass at half the threads, 2 CTAs/SM).
+// Measured per 2^27 elements: 2^13 407 us vs 447 us with 16 per thread;
+// 2^14 538 us vs 550 us.
+#ifndef B300_ROWS_RT32_MASK
+#define B300_ROWS_RT32_MASK ((1 << 13) | (1 << 14))
+#endif
+constexpr int rows_rt(int logn) { return logn >= 5 && ((B300_ROWS_RT32_MASK >> logn) & 1) ? 32 : 16; }
+constexpr int rows_tpc_rt(int logn) {
+    const int t = logn >= 4 ? (1 << logn) / rows_rt(logn) : 1;
     return t >= 256 ? 1 : 256 / t;
 }
 
 template <int LOGN>
 cudaError_t rows_prepare_l() {
-    constexpr int TPC = rows_default_tpc(LOGN);
-    const int sm = RowsCfg<LOGN, TPC>::SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_rows_pow2<LOGN, TPC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    constexpr int RT = rows_rt(LOGN), TPC = rows_tpc_rt(LOGN);
+    const int sm = RowsCfg<LOGN, TPC, RT>::SMEM;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_rows_pow2<LOGN, TPC, false, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_rows_pow2<LOGN, TPC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return cudaFuncSetAttribute(k_rows_pow2<LOGN, TPC, true, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 template <int LOGN>
 cudaError_t rows_launch_l(bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw, cudaStream_t st) {
-    constexpr int TPC = rows_default_tpc(LOGN);
-    using CF = RowsCfg<LOGN, TPC>;
+    constexpr int RT = rows_rt(LOGN), TPC = rows_tpc_rt(LOGN);
+    using CF = RowsCfg<LOGN, TPC, RT>;
     unsigned g;
     if (nrows <= 0) return cudaSuccess;
     if (grid_of(nrows, TPC, &g) != cudaSuccess) return cudaErrorInvalidConfiguration;
-    if (inv) k_rows_pow2<LOGN, TPC, true><<<g, CF::THREADS, CF::SMEM, st>>>(in, out, nrows, tw);
-    else k_rows_pow2<LOGN, TPC, false><<<g, CF::THREADS, CF::SMEM, st>>>(in, out, nrows, tw);
+    if (inv) k_rows_pow2<LOGN, TPC, true, RT><<<g, CF::THREADS, CF::SMEM, st>>>(in, out, nrows, tw);
+    else k_rows_pow2<LOGN, TPC, false, RT><<<g, CF::THREADS, CF::SMEM, st>>>(in, out, nrows, tw);
     return cudaGetLastError();
 }
 

@@ -28,10 +28,11 @@ namespace b300fft {
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
-template <int LOGN>
+// RT: elements per thread (16, or 32 = two radix-16 butterflies per pass).
+template <int LOGN, int RT = 16>
 struct P2Plan {
     static constexpr int N = 1 << LOGN;
-    static constexpr int R = N >= 16 ? 16 : N;  // elements per thread
+    static constexpr int R = N >= RT ? RT : (N >= 16 ? 16 : N);  // elements per thread
     static constexpr int T = N / R;             // threads per transform
     static constexpr int NP16 = N >= 16 ? LOGN / 4 : 0;
     static constexpr int REM = N >= 16 ? LOGN % 4 : 0;
@@ -109,23 +110,26 @@ __device__ __forceinline__ void dft_at(float2* v) {
 template <class PL, int P, bool INV>
 __device__ __forceinline__ void pass_compute(float2 (&v)[PL::R], int b0, const float2* __restrict__ tw) {
     constexpr int Rp = PL::radix(P), Q = PL::R / Rp, Ns = PL::ns(P);
-    if constexpr (P > 0 && Rp == 16 && Q == 1 && kTwiddleLoads6) {
+    if constexpr (P > 0 && Rp == 16 && kTwiddleLoads6) {
         // six table loads (W^k, W^2k, W^3k, W^4k, W^8k, W^12k); the other nine
         // twiddles are one complex product of two table values each
-        const float2* tp = tw + PL::twoff(P) + (b0 & (Ns - 1));
-        float2 w[16];
-        w[1] = __ldg(tp);
-        w[2] = __ldg(tp + Ns);
-        w[3] = __ldg(tp + 2 * Ns);
-        w[4] = __ldg(tp + 3 * Ns);
-        w[8] = __ldg(tp + 7 * Ns);
-        w[12] = __ldg(tp + 11 * Ns);
 #pragma unroll
-        for (int h = 4; h <= 12; h += 4)
+        for (int q = 0; q < Q; ++q) {
+            const float2* tp = tw + PL::twoff(P) + ((b0 + q * PL::T) & (Ns - 1));
+            float2 w[16];
+            w[1] = __ldg(tp);
+            w[2] = __ldg(tp + Ns);
+            w[3] = __ldg(tp + 2 * Ns);
+            w[4] = __ldg(tp + 3 * Ns);
+            w[8] = __ldg(tp + 7 * Ns);
+            w[12] = __ldg(tp + 11 * Ns);
 #pragma unroll
-            for (int l = 1; l <= 3; ++l) w[h + l] = cmul(w[h], w[l]);
+            for (int h = 4; h <= 12; h += 4)
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], w[r]);
+                for (int l = 1; l <= 3; ++l) w[h + l] = cmul(w[h], w[l]);
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[q + Q * r] = twmul<INV>(v[q + Q * r], w[r]);
+        }
     } else if constexpr (P > 0) {
         const float2* twp = tw + PL::twoff(P);
 #pragma unroll
@@ -234,17 +238,17 @@ __device__ __forceinline__ void run_passes_to_last(float2 (&v)[PL::R], int t, fl
 
 // Rows tile: TPC contiguous transforms of length N ([TPC][N] at src/dst);
 // rows >= nrows are skipped (their threads still take part in the barriers).
-template <int LOGN, int TPC>
+template <int LOGN, int TPC, int RT = 16>
 struct RowsCfg {
-    using PL = P2Plan<LOGN>;
+    using PL = P2Plan<LOGN, RT>;
     static constexpr int THREADS = PL::T * TPC;
     static constexpr int SMEM = (PL::NPASS > 1 ? PL::PADDED * TPC : 0) * 8;
 };
 
-template <int LOGN, int TPC, bool INV, Ld LK, St SK>
+template <int LOGN, int TPC, bool INV, Ld LK, St SK, int RT = 16>
 __device__ __forceinline__ void rows_tile(const float2* __restrict__ src, float2* __restrict__ dst, int nrows,
                                           const float2* __restrict__ tw, float2* smem, uint64_t pol) {
-    using PL = typename RowsCfg<LOGN, TPC>::PL;
+    using PL = typename RowsCfg<LOGN, TPC, RT>::PL;
     const int t = threadIdx.x & (PL::T - 1);
     const int sub = threadIdx.x / PL::T;
     const bool ok = sub < nrows;
@@ -389,14 +393,16 @@ __device__ __forceinline__ void cols_tile(const float2* __restrict__ src, float2
 // ---------------------------------------------------------------------------
 // One-tile-per-CTA kernels.
 // ---------------------------------------------------------------------------
-template <int LOGN, int TPC, bool INV>
-__global__ void __launch_bounds__(RowsCfg<LOGN, TPC>::THREADS, 1024 / RowsCfg<LOGN, TPC>::THREADS)
+// RT = 32 (two butterflies per thread) takes ~115 registers: 512 threads/SM.
+template <int LOGN, int TPC, bool INV, int RT = 16>
+__global__ void __launch_bounds__(RowsCfg<LOGN, TPC, RT>::THREADS,
+                                  (RT == 16 ? 1024 : 512) / RowsCfg<LOGN, TPC, RT>::THREADS)
 k_rows_pow2(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     const int64_t row0 = (int64_t)blockIdx.x * TPC;
     const int64_t left = nrows - row0;
-    rows_tile<LOGN, TPC, INV, Ld::Stream, St::Stream>(in + row0 * (1 << LOGN), out + row0 * (1 << LOGN),
-                                                      left < TPC ? (int)left : TPC, tw, smem, 0);
+    rows_tile<LOGN, TPC, INV, Ld::Stream, St::Stream, RT>(in + row0 * (1 << LOGN), out + row0 * (1 << LOGN),
+                                                          left < TPC ? (int)left : TPC, tw, smem, 0);
 }
 
 // nrows = items * n1 rows; the CTA's TPC rows are consecutive k1 of one item.
