@@ -143,11 +143,12 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle arm (bounded sample)
 # --------------------------------------------------------------------------
-def oracle_sample(budget_elems: int = 1 << 21, sizes=None):
+def oracle_sample(budget_elems: int = 1 << 21, sizes=None, threads: int = 0):
     """Time the FP64 oracle (forward + inverse) on min(batch, budget/N) transforms
-    of each sweep size; returns (GFLOP/s, seconds, threads, description)."""
+    of each sweep size on `threads` host threads (0: all cores); returns
+    (GFLOP/s, seconds, threads, description)."""
     import oracle
-    threads = oracle.num_cpus()
+    threads = threads or oracle.num_cpus()
     sizes = sizes or inputs.sweep_sizes(TOTAL_LOG2, LO, HI)
     fl, secs = 0.0, 0.0
     for k, n, b in sizes:
@@ -158,7 +159,7 @@ def oracle_sample(budget_elems: int = 1 << 21, sizes=None):
         oracle.fft(y, +1, threads)
         secs += time.perf_counter() - t0
         fl += 2 * 5.0 * n * k * m
-    desc = (f"FP64 C oracle (radix-2), fwd+inv of min(batch, 2^21/N) transforms per size "
+    desc = (f"FP64 C oracle (radix-2), fwd+inv of min(batch, 2^{int(math.log2(budget_elems))}/N) transforms per size "
             f"N=2^{LO}..2^{HI}, {threads} threads")
     return fl / secs / 1e9, secs, threads, desc
 
@@ -189,6 +190,33 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def fma_ceiling():
+    """Measured FP32 FMA rate of the GPU (the library's probe kernel: 16
+    independent chains per thread, 8 CTAs of 256 threads per SM), timed alone
+    outside the sweep's timed region.  Context for the butterflies' arithmetic,
+    which the HBM roofline does not cover."""
+    import torch
+    from paper_1203_4938_b300 import fft as F
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, iters = sms * 8, 1 << 14
+    out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        F.fma_probe(blocks, iters, out)
+    best = None
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, flops = F.fma_probe(blocks, iters, out)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        best = t if best is None else min(best, t)
+    if not bool((out == 120.0 + 16.0 * iters).all()):
+        raise RuntimeError("FMA probe returned wrong values")
+    return flops / best / 1e12
+
+
+
 def run_gpu(args):
     import torch
     from paper_1203_4938_b300 import build as B
@@ -288,6 +316,7 @@ def run_gpu(args):
 
     fl = sum(2 * 5.0 * n * b * k for k, n, b in sizes)
     value = job_throughput(fl, world, ms)
+    fma_tflops = fma_ceiling()
 
     # end to end through the public API: pinned host input -> device, fwd+inv, result -> host
     e2e = None
@@ -323,8 +352,10 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         gf, secs, threads, desc = oracle_sample(1 << 19 if args.quick else 1 << 21)
+        gf1, secs1, _, desc1 = oracle_sample(1 << 15 if args.quick else 1 << 16, threads=1)
         cpu = {"value": gf, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc,
-               "seconds": secs}
+               "seconds": secs, "one_core": {"value": gf1, "unit": "GFLOP/s", "cores": 1, "sample": desc1,
+                                             "seconds": secs1}}
 
     if rank == 0:
         kname = plans[di].describe()
@@ -344,6 +375,10 @@ def run_gpu(args):
                          "kernel_time_share": share, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
                          if "hbm_gbs" in peaks else "fallback 6.4 TB/s"},
             "clocks": clocks,
+            "alu_context": {"fp32_fma_tflops_measured": fma_tflops,
+                            "sweep_nominal_tflops": value / 1e3, "nominal_frac": value / 1e3 / fma_tflops,
+                            "note": "nominal 5N log2 N flops per transform against the measured FP32 FMA "
+                                    "rate (probe kernel); the sweep is bounded by HBM, not by this"},
             "per_size_ms": {f"2^{sizes[i][0]}": sum(statistics.mean(per[(i, kk)]) for kk in
                                                    range(plans[i].kernel_count)) * 2 for i in range(len(sizes))},
         }

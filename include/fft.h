@@ -133,6 +133,15 @@ FFT_API fft_status fft_spectrum_product(const void *a, const void *b, void *out,
 FFT_API fft_status fft_image_steps(const void *rgb, int64_t batch, int64_t h, int64_t w, float ux, float uy,
                                    void *y, void *cb, void *cr, void *d, void *stream);
 
+/* FP32 FMA throughput probe (measurement aid, not part of a transform): the
+ * non-tensor arithmetic ceiling that the butterfly work is compared with.
+ * Launches `blocks` CTAs of 256 threads; each thread runs 16 independent
+ * FMA chains for `iters` rounds, i.e. blocks * 256 * 16 * iters FMAs
+ * (2 flops each).  out: device float32 [blocks * 256], 4-byte aligned; every
+ * element is set to 120 + 16 * iters (exact).  1 <= blocks <= 2^24,
+ * 1 <= iters <= 2^20 (else FFT_ERR_INVALID_ARG).  Asynchronous on `stream`. */
+FFT_API fft_status fft_probe_fma(void *out, int64_t blocks, int64_t iters, void *stream);
+
 /* Status of the last fft_plan_create* call on this host thread. */
 FFT_API fft_status fft_last_error(void);
 

@@ -42,7 +42,8 @@ PRECISIONS = {"fp32": FFT_FP32, "tc_fp16": FFT_TC_FP16, "tc_bf16": FFT_TC_BF16,
 EXPORTS = ("fft_plan_create", "fft_plan_create_ragged", "fft_last_error", "fft_exec",
            "fft_plan_check", "fft_plan_destroy", "fft_plan_workspace_bytes", "fft_status_string",
            "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size",
-           "fft_exec_pow2_static", "fft_plan_create_real", "fft_spectrum_product", "fft_image_steps")
+           "fft_exec_pow2_static", "fft_plan_create_real", "fft_spectrum_product", "fft_image_steps",
+           "fft_probe_fma")
 
 _lock = threading.Lock()
 _lib = None
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fft_image_steps.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                         ctypes.c_float, vp, vp, vp, vp, vp]
         lib.fft_image_steps.restype = ctypes.c_int
+        lib.fft_probe_fma.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp]
+        lib.fft_probe_fma.restype = ctypes.c_int
         lib.fft_plan_create_real.argtypes = [ctypes.c_int64, ctypes.c_int64]
         lib.fft_plan_create_real.restype = vp
         lib.fft_last_error.argtypes = []
@@ -138,6 +141,24 @@ def fft_image_steps(rgb_ptr: int, batch: int, h: int, w: int, ux: float, uy: flo
                     cr_ptr: int, d_ptr: int, stream: int = 0) -> int:
     return int(load().fft_image_steps(rgb_ptr, int(batch), int(h), int(w), float(ux), float(uy), y_ptr, cb_ptr,
                                       cr_ptr, d_ptr, stream or None))
+
+
+def fft_probe_fma(out_ptr: int, blocks: int, iters: int, stream: int = 0) -> int:
+    return int(load().fft_probe_fma(out_ptr, int(blocks), int(iters), stream or None))
+
+
+def fma_probe(blocks: int, iters: int, out=None):
+    """Run the FP32 FMA probe on the current stream; returns (out, flops).
+    out: float32 CUDA tensor of blocks * 256 elements (allocated if None)."""
+    import torch
+    if out is None:
+        out = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or not out.is_cuda or out.numel() < blocks * 256:
+        raise ValueError("out must be a CUDA float32 tensor of blocks * 256 elements")
+    st = fft_probe_fma(out.data_ptr(), blocks, iters, torch.cuda.current_stream().cuda_stream)
+    if st != 0:
+        raise FFTError(st, "fft_probe_fma")
+    return out, 2.0 * 16 * 256 * blocks * iters
 
 
 def fft_last_error() -> int:

@@ -75,3 +75,13 @@ def test_ragged_invalid_arguments(lib):
     assert F.fft_last_error() == F.FFT_ERR_INVALID_ARG
     assert lib.fft_plan_create_ragged(None, 3, 0) is None
     assert F.fft_last_error() == F.FFT_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("out,blocks,iters,status", [
+    (0, 1, 1, F.FFT_ERR_INVALID_ARG), (256, 0, 1, F.FFT_ERR_INVALID_ARG), (256, 1, 0, F.FFT_ERR_INVALID_ARG),
+    (256, 1, (1 << 20) + 1, F.FFT_ERR_INVALID_ARG), (256, (1 << 24) + 1, 1, F.FFT_ERR_INVALID_ARG),
+    (258, 1, 1, F.FFT_ERR_MISALIGNED),
+])
+def test_fma_probe_argument_errors(lib, out, blocks, iters, status):
+    # rejected before any launch: the pointer is never dereferenced
+    assert F.fft_probe_fma(out, blocks, iters) == status
