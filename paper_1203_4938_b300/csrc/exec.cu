@@ -16,6 +16,19 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
         case PlanKind::Rows:
             if (want(0)) e = launch_rows(p->logn_a, inv, in, out, p->batch, p->d_tables + p->off_a, st);
             break;
+        case PlanKind::FourStepMixed: {
+            const int64_t n1 = int64_t(p->mix_m) << p->logn_a, n2 = int64_t(1) << p->logn_b;
+            if (want(0))
+                e = launch_cols_mixed(p->mix_m, p->logn_a, inv, in, p->d_work, n2, p->batch, p->d_tables + p->off_a,
+                                      p->d_tables + p->off_lo, p->d_tables + p->off_hi, p->sh, st);
+            if (e == cudaSuccess && want(1))
+                e = launch_rowsT(p->logn_b, p->rowsT_tpc, inv, p->d_work, out, p->batch * n1, p->d_tables + p->off_b,
+                                 n1, st);
+            break;
+        }
+        case PlanKind::RowsMixed:
+            if (want(0)) e = launch_rows_mixed(p->mix_m, p->logn_a, inv, in, out, p->batch, p->d_tables, st);
+            break;
         case PlanKind::FourStep: {
             const int64_t n1 = int64_t(1) << p->logn_a, n2 = int64_t(1) << p->logn_b;
             if (want(0))

@@ -166,10 +166,12 @@ fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
 // Persistent three-stage: N = N1 * M1 * M2 with 2^6 .. 2^8-point stages.
 // kThree[log2 N] = {log2 N1, log2 M1, log2 M2, chunk MiB, default on}.
 // Measured on a B300 with 2^26 elements per exec: faster than the two-pass
-// persistent four-step from 2^21 on (2^19 and 2^20 are slower).
+// persistent four-step from 2^21 on (2^19 and 2^20 are slower).  Chunks of
+// 32 MiB (one or two transforms): 2^21 494 us vs 503 us with 128 MiB chunks;
+// letting the A stage run more than one chunk ahead was slower at every size.
 static const int kThree[25][5] = {
     {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
-    {6, 6, 7, 128, 0}, {6, 7, 7, 128, 0}, {7, 7, 7, 128, 1}, {7, 7, 8, 128, 1},
+    {6, 6, 7, 128, 0}, {6, 7, 7, 128, 0}, {7, 7, 7, 32, 1}, {7, 7, 8, 32, 1},
     {8, 7, 8, 32, 1}, {8, 8, 8, 32, 1}};
 
 bool three_preferred(int logn) { return logn >= 0 && logn <= 24 && kThree[logn][4] != 0; }
@@ -483,6 +485,82 @@ fft_plan finish(fft_plan_s* p) {
 
 namespace b300fft {
 
+// N = M * 2^k > 4096 with M = 3, 5, 7.
+bool mixed_fourstep_length(int64_t n, int* m, int* k) {
+    if (n <= 4096) return false;
+    for (int mm : {3, 5, 7}) {
+        if (n % mm) continue;
+        const int64_t q = n / mm;
+        if (q & (q - 1)) continue;
+        int kk = 0;
+        while ((int64_t(1) << kk) < q) ++kk;
+        *m = mm;
+        *k = kk;
+        return true;
+    }
+    return false;
+}
+
+// L = M * 2^K <= 4096 (M = 3, 5, 7): the compile-time single-pass kernel.
+fft_status build_mixed_1d(fft_plan_s* p, int m, int k) {
+    const int entries = mixed_table_entries(m, k);
+    if (entries < 0) return FFT_ERR_UNSUPPORTED;
+    fft_status s = alloc_tables(p, (size_t)entries);
+    if (s != FFT_OK) return s;
+    if (entries > 0 && gen_mixed_table(p->d_tables, m, k, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    p->kind = PlanKind::RowsMixed;
+    p->mix_m = m;
+    p->logn_a = k;
+    p->kernels = 1;
+    std::snprintf(p->desc, sizeof p->desc, "rows-mixed N=%lld = %d x 2^%d lines/CTA=%d threads=256",
+                  (long long)p->len[0], m, k, mixed_lines_per_cta(m, k));
+    return FFT_OK;
+}
+
+// N = M * 2^k > 4096 (M = 3, 5, 7): four-step N = N1 * N2 with N2 = 2^b,
+// b = min(12, k - 2) (at least 4 transposed rows per CTA), N1 = M * 2^(k - b)
+// columns by the compile-time mixed kernel, then the power-of-two
+// transposed rows.  Returns FFT_ERR_UNSUPPORTED where no column kernel fits.
+fft_status build_mixed_fourstep(fft_plan_s* p, int m, int k) {
+    const int b = k - 2 < 12 ? k - 2 : 12, a = k - b;
+    const int c = mixed_cols_width(m, a);
+    if (b < 6 || c == 0 || c > (1 << b)) return FFT_ERR_UNSUPPORTED;
+    const int64_t n1 = int64_t(m) << a, n2 = int64_t(1) << b, n = n1 * n2;
+    int tpc = 16;
+    while (tpc > 2 && (rowsT_threads(b, tpc) > 1024 || n1 % tpc != 0)) tpc /= 2;
+    if (n1 % tpc != 0 || rowsT_threads(b, tpc) > 1024) return FFT_ERR_UNSUPPORTED;
+    int lg = 0;
+    while ((int64_t(1) << lg) < n) ++lg;
+    p->sh = (lg + 1) / 2;
+    const int ea = mixed_table_entries(m, a), eb = pow2_table_entries(b);
+    if (ea < 0) return FFT_ERR_UNSUPPORTED;
+    const int64_t elo = int64_t(1) << p->sh, ehi = (n + elo - 1) / elo;
+    p->off_a = 0;
+    p->off_b = (size_t)ea;
+    p->off_lo = p->off_b + (size_t)eb;
+    p->off_hi = p->off_lo + (size_t)elo;
+    fft_status s = alloc_tables(p, p->off_hi + (size_t)ehi);
+    if (s != FFT_OK) return s;
+    if (ea > 0 && gen_mixed_table(p->d_tables + p->off_a, m, a, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_pow2_table(p->d_tables + p->off_b, b, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_lo, elo, 1, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (gen_root_table(p->d_tables + p->off_hi, ehi, elo, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+    if (rowsT_prepare(b, tpc) != cudaSuccess) return FFT_ERR_CUDA;
+    p->work_bytes = (size_t)n * (size_t)p->batch * sizeof(float2);
+    if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
+    p->kind = PlanKind::FourStepMixed;
+    p->mix_m = m;
+    p->logn_a = a;
+    p->logn_b = b;
+    p->cols_c = c;
+    p->rowsT_tpc = tpc;
+    p->kernels = 2;
+    std::snprintf(p->desc, sizeof p->desc,
+                  "fourstep-mixed N=%lld = (%d x 2^%d, %d columns/CTA) x 2^%d (tpc=%d)", (long long)n, m, a, c, b,
+                  tpc);
+    return FFT_OK;
+}
+
 // Non-power-of-two 1-D lengths: mixed radix 2/3/4/5/7/8/16 (single tile or
 // four-step) or Bluestein, through the stage-graph executor.
 fft_status build_generic_1d(fft_plan_s* p) {
@@ -540,8 +618,16 @@ fft_plan fft_plan_create(int dims, const int64_t* lengths, int64_t batch, int pr
         s = build_tc_plan(p);
     } else if (dims == 1) {
         const int l = ilog2_exact(lengths[0]);
+        int mm = 0, kk = 0;
         if (l >= 0) s = build_pow2_1d(p, l);
-        else s = build_generic_1d(p);
+        else if (mixed_supported(lengths[0], &mm, &kk) && env_int("B300FFT_MIXED", 1) != 0)
+            s = build_mixed_1d(p, mm, kk);
+        else if (mixed_fourstep_length(lengths[0], &mm, &kk) && env_int("B300FFT_MIXED", 1) != 0) {
+            s = build_mixed_fourstep(p, mm, kk);  // unsupported splits return before allocating
+            if (s == FFT_ERR_UNSUPPORTED) s = build_generic_1d(p);
+        } else {
+            s = build_generic_1d(p);
+        }
     } else {
         const int lh = ilog2_exact(lengths[0]), lw = ilog2_exact(lengths[1]);
         if (lh >= 0 && lw >= 0) s = build_pow2_2d(p, lh, lw);

@@ -212,7 +212,10 @@ __device__ void g_tile_dir(const GStage& st, const GShape& sh, const float2* __r
     // flight per thread before their shared-memory stores
     const int tot = nl * L;
     const FastDiv by_nl((uint32_t)nl), by_L((uint32_t)L);
-    constexpr int U = 4;
+#ifndef B300_G_LOADS
+#define B300_G_LOADS 8
+#endif
+    constexpr int U = B300_G_LOADS;
     for (int e0 = threadIdx.x; e0 < tot; e0 += U * kGThreads) {
         float2 v[U];
         int dst[U];

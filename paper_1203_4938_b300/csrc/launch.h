@@ -31,6 +31,20 @@ cudaError_t gen_bluestein_filter(float2* out, int64_t n, int64_t M, bool inverse
 int rows_tpc(int logn);
 int rows_threads(int logn);
 cudaError_t rows_prepare(int logn);  // raise the dynamic shared-memory limit
+// --- single-pass mixed radix, L = M * 2^K <= 4096, M = 3, 5, 7 (k_mixed.cu) ----
+bool mixed_supported(int64_t n, int* m, int* k);
+int mixed_table_entries(int m, int k);
+int mixed_lines_per_cta(int m, int k);
+cudaError_t gen_mixed_table(float2* tw, int m, int k, cudaStream_t st);
+cudaError_t launch_rows_mixed(int m, int k, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                              cudaStream_t st);
+// Four-step first pass for N = M * 2^a * S2: columns of length M * 2^a over
+// `items` row-major [M * 2^a][S2] arrays, mixed_cols_width(m, a) columns per
+// CTA (0: no kernel for that length), times W_N^{n2 k1} from (lo, hi, sh).
+int mixed_cols_width(int m, int a);
+cudaError_t launch_cols_mixed(int m, int a, bool inv, const float2* in, float2* out, int64_t S2, int64_t items,
+                              const float2* tw, const float2* lo, const float2* hi, int sh, cudaStream_t st);
+
 cudaError_t launch_rows(int logn, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
                         cudaStream_t st);
 

@@ -18,6 +18,8 @@ enum class PlanKind : int {
     Cluster,          // one transform per thread-block cluster, DSMEM exchanges, one HBM round trip
     TwoD,      // rows pass then in-place columns pass
     TwoDPersist,  // both 2-D passes in one persistent launch, L2-resident chunks of images
+    RowsMixed, // single-pass mixed-radix rows kernel, L = M * 2^K <= 4096 (M = 3, 5, 7)
+    FourStepMixed, // N = (M * 2^a) * 2^b: mixed columns kernel + power-of-two transposed rows
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
     Ragged,    // persistent work-queue kernel over uneven lengths
@@ -42,6 +44,7 @@ struct fft_plan_s {
 
     // power-of-two kernels
     int logn_a = 0, logn_b = 0, sh = 0;
+    int mix_m = 0;  // RowsMixed: L = mix_m * 2^logn_a
     int cols_c = 0;     // columns kernel width
     int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA
 
