@@ -24,6 +24,7 @@
 // atomic counter in an order where dependencies always come first.
 #pragma once
 #include "butterfly.cuh"
+#include "mixed.cuh"
 #include "persist.cuh"
 
 namespace b300fft {
@@ -56,7 +57,9 @@ struct GStage {
     int pre, post;
     int sh;
     int tmpl;  // > 0: templated tiles: 2 * log2 N + (0: A, 1: B) of a power-of-two four-step,
-               // or 100 + log2 N2: second stage (rows of 2^L2) of a mixed-length four-step
+               // 100 + log2 N2: second stage (rows of 2^L2) of a mixed-length four-step,
+               // 1000 + 16 M + K: single-tile lines of M * 2^K (compile-time mixed radix),
+               // 2000 + 16 M + A: four-step first stage, columns of M * 2^A (compile-time)
     int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
     int64_t pre_tab, post_tab;             // table offsets in the pool
@@ -332,8 +335,100 @@ __device__ __forceinline__ void g_rowsT_stage(const GExecArgs& a, const GTransfo
     else rowsT_tile<L2, TPC, false, Ld::Cg, St::Stream>(src, dst, (int64_t)st.nlines, a.pool + st.post_tab, smem, pol);
 }
 
+// Lines of the compile-time mixed-radix tiles: kGMixLines(L) per tile, the
+// element offset of each line in shared memory past the tile's buffer.
+__host__ __device__ constexpr int kGMixLines(int L) { return 4096 / L < kGMaxLines ? 4096 / L : kGMaxLines; }
+constexpr int kGMixOffF2 = 6144;  // float2 offset of the line-offset table in the dynamic buffer
+static_assert(kGMixOffF2 * 8 + kGMaxLines * 8 <= kGSmem, "line offsets fit the executor's shared memory");
+
+template <int L>
+struct MixRowsAt {  // line l, element e at base + off[l] + e
+    static constexpr bool LINE_FAST = false;
+    const float2* in;
+    float2* out;
+    const int64_t* off;
+    __device__ __forceinline__ float2 load(int line, int e) const { return __ldcs(in + off[line] + e); }
+    __device__ __forceinline__ void store(int line, int e, float2 v) const { __stcs(out + off[line] + e, v); }
+};
+
+// Single-tile stage of lines of M * 2^K (uniform rows or separate transforms):
+// line l of the stage starts at line_off[line_tab + l] (line_tab >= 0) or at
+// l * ls.  Not inlined: each tile shape gets its own register allocation.
+template <int M, int K>
+__device__ __noinline__ void g_mixed_rows(const float2* gin, float2* gout, const int64_t* __restrict__ line_off,
+                                          int64_t line_tab, int64_t ls, int nlines, int tile, int inv,
+                                          const float2* __restrict__ tw, float2* smem) {
+    using MP = MixPlan<M, K, kGMixLines(M << K)>;
+    static_assert(MP::SMEM <= kGMixOffF2 * 8, "tile buffer below the line-offset table");
+    int64_t* s_off = reinterpret_cast<int64_t*>(smem + kGMixOffF2);
+    const int line0 = tile * MP::NL;
+    const int nl = min(MP::NL, nlines - line0);
+    for (int l = threadIdx.x; l < nl; l += kGThreads)
+        s_off[l] = line_tab >= 0 ? __ldg(line_off + line_tab + line0 + l) : (int64_t)(line0 + l) * ls;
+    __syncthreads();
+    const MixRowsAt<MP::L> io{gin, gout, s_off};
+    if (inv) mix_pass<MP, 0, true>(io, smem, nl, tw);
+    else mix_pass<MP, 0, false>(io, smem, nl, tw);
+}
+
+// Four-step first stage of N = (M * 2^A) * S2: NL adjacent columns, W_N twiddle out.
+template <int M, int A, int NL>
+__device__ __noinline__ void g_mixed_cols(const float2* gin, float2* gout, int64_t S2, int tile, int inv,
+                                          const float2* __restrict__ tw, const float2* __restrict__ lo,
+                                          const float2* __restrict__ hi, int sh, float2* smem) {
+    using MP = MixPlan<M, A, NL>;
+    const int64_t col0 = (int64_t)tile * NL;
+    if (inv) {
+        const MixCols<true> io{gin + col0, gout + col0, S2, (uint32_t)col0, lo, hi, sh};
+        mix_pass<MP, 0, true>(io, smem, NL, tw);
+    } else {
+        const MixCols<false> io{gin + col0, gout + col0, S2, (uint32_t)col0, lo, hi, sh};
+        mix_pass<MP, 0, false>(io, smem, NL, tw);
+    }
+}
+
+// Compile-time mixed tiles of the stage graph (the lengths of the batched
+// mixed-radix kernels; columns M * 2^A with the same widths).
+#define B300_G_MIXED_ROWS(X)                                                                                    \
+    X(3, 0) X(3, 1) X(3, 2) X(3, 3) X(3, 4) X(3, 5) X(3, 6) X(3, 7) X(3, 8) X(3, 9) X(3, 10) X(5, 0) X(5, 1)    \
+    X(5, 2) X(5, 3) X(5, 4) X(5, 5) X(5, 6) X(5, 7) X(5, 8) X(5, 9) X(7, 0) X(7, 1) X(7, 2) X(7, 3) X(7, 4)     \
+    X(7, 5) X(7, 6) X(7, 7) X(7, 8) X(7, 9)
+#define B300_G_MIXED_COLS(X)                                                                           \
+    X(3, 2, 256) X(3, 3, 128) X(3, 4, 64) X(3, 5, 32) X(3, 6, 16) X(3, 7, 8) X(5, 2, 128) X(5, 3, 64)      \
+    X(5, 4, 32) X(5, 5, 16) X(5, 6, 8) X(7, 2, 128) X(7, 3, 64) X(7, 4, 32) X(7, 5, 16) X(7, 6, 8)
+
+__device__ __forceinline__ void g_mixed_tile(const GExecArgs& a, const GTransform& x, const GStage& st, int tile,
+                                             float2* smem) {
+    const float2* gin = g_buf_in(a, x, st.in_buf);
+    float2* gout = g_buf_out(a, x, st.out_buf);
+    const float2* tw = a.pool + st.pre_tab;
+    switch (st.tmpl) {
+#define B300_R(M, K)                                                                                          \
+    case 1000 + 16 * M + K:                                                                                   \
+        g_mixed_rows<M, K>(gin, gout, a.line_off, st.line_tab, st.in_ls, st.nlines, tile, st.inv, tw, smem); \
+        break;
+        B300_G_MIXED_ROWS(B300_R)
+#undef B300_R
+#define B300_C(M, A, NL)                                                                                          \
+    case 2000 + 16 * M + A:                                                                                       \
+        g_mixed_cols<M, A, NL>(gin, gout, st.in_es, tile, st.inv, tw, a.pool + st.lo, a.pool + st.hi, st.sh, smem); \
+        break;
+        B300_G_MIXED_COLS(B300_C)
+#undef B300_C
+        default:
+            break;
+    }
+}
+
+template <bool MIX>
 __device__ __forceinline__ void g_pow2_tile(const GExecArgs& a, const GTransform& x, const GStage& st, int tile,
                                             float2* smem) {
+    if constexpr (MIX) {
+        if (st.tmpl >= 1000) {
+            g_mixed_tile(a, x, st, tile, smem);
+            return;
+        }
+    }
     if (st.tmpl >= 100) {  // 100 + L2: mixed four-step second stage
         switch (st.tmpl - 100) {
             case 7: g_rowsT_stage<7, 32>(a, x, st, tile, smem); break;
@@ -352,6 +447,7 @@ __device__ __forceinline__ void g_pow2_tile(const GExecArgs& a, const GTransform
 }
 
 // Run queue item p (tile of one stage of one transform).
+template <bool MIX>
 __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* smem, int* s_ok) {
     const uint64_t it = a.items[p];
     const int t = (int)(it >> 32);
@@ -379,7 +475,7 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
         if (!*s_ok) return;
     }
     if (st.tmpl) {
-        g_pow2_tile(a, x, st, tile, smem);
+        g_pow2_tile<MIX>(a, x, st, tile, smem);
     } else {
         const int line0 = tile * st.lpt;
         const int nl = min(st.lpt, st.nlines - line0);
@@ -398,13 +494,16 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
 }
 
 // Persistent executor (single = 0) or one launch per stage group (single = 1:
-// block b runs item item0 + b; the stream orders the stages).
+// block b runs item item0 + b; the stream orders the stages).  MIX: the plan
+// has compile-time mixed-radix stages (a separate kernel, so plans without
+// them keep the smaller kernel's register allocation).
+template <bool MIX>
 __global__ void __launch_bounds__(kGThreads, 3) k_gexec(GExecArgs a) {
     extern __shared__ float2 smem[];
     __shared__ int s_item[2];
     __shared__ int s_ok;
     if (a.single) {
-        g_run_item(a, a.item0 + blockIdx.x, smem, &s_ok);
+        g_run_item<MIX>(a, a.item0 + blockIdx.x, smem, &s_ok);
         return;
     }
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl, 1);
@@ -413,7 +512,7 @@ __global__ void __launch_bounds__(kGThreads, 3) k_gexec(GExecArgs a) {
         const int p = s_item[it];
         if (p >= a.nitems) break;
         if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.ctl, 1);
-        g_run_item(a, p, smem, &s_ok);
+        g_run_item<MIX>(a, p, smem, &s_ok);
     }
 }
 

@@ -24,6 +24,15 @@ int env_i(const char* name, int dflt) {
     return (v && *v) ? std::atoi(v) : dflt;
 }
 
+// The executor kernel a plan runs (with or without the compile-time mixed tiles).
+const void* gexec_fn(const GraphPlan* gp) {
+    return gp->mix ? (const void*)k_gexec<true> : (const void*)k_gexec<false>;
+}
+void launch_gexec(const GraphPlan* gp, int grid, const GExecArgs& a, cudaStream_t st) {
+    if (gp->mix) k_gexec<true><<<grid, kGThreads, kGSmem, st>>>(a);
+    else k_gexec<false><<<grid, kGThreads, kGSmem, st>>>(a);
+}
+
 bool is_smooth(int64_t n) {
     for (int p : {2, 3, 5, 7})
         while (n % p == 0) n /= p;
@@ -84,6 +93,15 @@ struct Builder {
     std::vector<RootTab> root_tabs;
     std::vector<BlueTab> blue_list;
     std::map<int, int64_t> pow2_tabs;  // log2 L -> offset of the templated tiles' Stockham table
+    std::map<int, int64_t> mixed_tabs;  // 64 M + K -> offset of the compile-time mixed tiles' table
+
+    int64_t mixed_table(int m, int k) {
+        auto it = mixed_tabs.find(64 * m + k);
+        if (it != mixed_tabs.end()) return it->second;
+        const int64_t o = alloc(std::max(1, mixed_table_entries(m, k)));
+        mixed_tabs[64 * m + k] = o;
+        return o;
+    }
 
     int64_t pow2_table(int logn) {
         auto it = pow2_tabs.find(logn);
@@ -142,6 +160,17 @@ struct Builder {
         return t;
     }
 };
+
+// Compile-time mixed tiles (B300FFT_G_MIXT=0 turns them off): lines of
+// L = M * 2^K <= 4096, and four-step columns of M * 2^A with a column width.
+bool mixed_rows_templated(int64_t n, int* m, int* k) {
+    return env_i("B300FFT_G_MIXT", 1) != 0 && mixed_supported(n, m, k);
+}
+bool mixed_cols_templated(int64_t n1, int64_t n2, int* m, int* a, int* width) {
+    if (env_i("B300FFT_G_MIXT", 1) == 0 || !mixed_supported(n1, m, a)) return false;
+    *width = mixed_cols_width(*m, *a);
+    return *width > 0 && n2 % *width == 0;
+}
 
 // Power-of-two lengths the stage graph runs with the templated tiles.
 bool pow2_templated(int64_t n) {
@@ -211,6 +240,13 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
                 s.line_tab = line_tab;
                 s.in_valid = s.out_valid = INT64_MAX;
             }
+            int mm = 0, kk = 0;
+            if (mixed_rows_templated(n, &mm, &kk)) {
+                s.tmpl = 1000 + 16 * mm + kk;
+                s.lpt = std::min(kGMixLines((int)n), std::max(1, (int)lines));
+                s.ntiles = (int)((lines + kGMixLines((int)n) - 1) / kGMixLines((int)n));
+                s.pre_tab = B.mixed_table(mm, kk);
+            }
             (d ? i : f).push_back(s);
         }
     } else if (pow2_templated(n)) {
@@ -264,6 +300,13 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
             a.lo = tabs.first;
             a.hi = tabs.second;
             a.sh = shs;
+            int mm = 0, aa = 0, width = 0;
+            if (mixed_cols_templated(n1, n2, &mm, &aa, &width)) {
+                a.tmpl = 2000 + 16 * mm + aa;
+                a.lpt = width;
+                a.ntiles = (int)(n2 / width);
+                a.pre_tab = B.mixed_table(mm, aa);
+            }
             GStage b = base_stage(sb, (int)n1, lines_per_tile((int)n2, cfg.lpt_b), d);
             b.in_buf = G_BUF_W1;
             b.out_buf = G_BUF_OUT;
@@ -723,6 +766,10 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
         if (gen_root_table(gp->pool + t.off, t.count, t.mult, t.n, st) != cudaSuccess) return FFT_ERR_CUDA;
     for (auto& t : B.pow2_tabs)
         if (gen_pow2_table(gp->pool + t.second, t.first, st) != cudaSuccess) return FFT_ERR_CUDA;
+    for (auto& t : B.mixed_tabs)
+        if (mixed_table_entries(t.first / 64, t.first % 64) > 0 &&
+            gen_mixed_table(gp->pool + t.second, t.first / 64, t.first % 64, st) != cudaSuccess)
+            return FFT_ERR_CUDA;
     if (!B.blue_list.empty()) {
         int64_t maxM = 0;
         for (auto& b : B.blue_list) maxM = std::max(maxM, b.M);
@@ -751,10 +798,13 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
     if (cudaMalloc(&gp->ctl, sizeof(int) * (size_t)(1 + ctr)) != cudaSuccess) return FFT_ERR_ALLOC;
     gp->work_bytes = (size_t)woff * sizeof(float2);
     if (woff > 0 && cudaMalloc(&gp->work, gp->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
-    if (cudaFuncSetAttribute(k_gexec, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem) != cudaSuccess)
+    gp->mix = false;
+    for (const GStage& g : B.st_f) gp->mix = gp->mix || g.tmpl >= 1000;
+    const void* kfn = gexec_fn(gp);
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem) != cudaSuccess)
         return FFT_ERR_CUDA;
     int bps = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_gexec, kGThreads, kGSmem) != cudaSuccess || bps < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, kGThreads, kGSmem) != cudaSuccess || bps < 1)
         return FFT_ERR_CUDA;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -810,7 +860,7 @@ cudaError_t ensure_graph(GraphPlan* gp, bool inv, const GExecArgs& a) {
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(1 + gp->ncounters), cs);
-        k_gexec<<<gp->grid, kGThreads, kGSmem, cs>>>(a);
+        launch_gexec(gp, gp->grid, a, cs);
         e = cudaStreamEndCapture(cs, &gp->graph[d]);
     }
     cudaStreamDestroy(cs);
@@ -835,7 +885,7 @@ fft_status graph_plan_exec(GraphPlan* gp, const float2* in, float2* out, bool in
     if (per_stage) {
         for (auto& g : gp->groups) {
             GExecArgs a = make_args(gp, in, out, inv, d_status, 1, g.first);
-            k_gexec<<<g.second - g.first, kGThreads, kGSmem, st>>>(a);
+            launch_gexec(gp, g.second - g.first, a, st);
             e = cudaGetLastError();
             if (e != cudaSuccess) return FFT_ERR_CUDA;
         }
@@ -849,7 +899,7 @@ fft_status graph_plan_exec(GraphPlan* gp, const float2* in, float2* out, bool in
         if (ensure_graph(gp, inv, a) != cudaSuccess) return FFT_ERR_CUDA;
         cudaKernelNodeParams kp{};
         void* params[1] = {&a};
-        kp.func = (void*)k_gexec;
+        kp.func = const_cast<void*>(gexec_fn(gp));
         kp.gridDim = dim3(gp->grid);
         kp.blockDim = dim3(kGThreads);
         kp.sharedMemBytes = kGSmem;
@@ -860,7 +910,7 @@ fft_status graph_plan_exec(GraphPlan* gp, const float2* in, float2* out, bool in
     }
     e = cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(1 + gp->ncounters), st);
     if (e == cudaSuccess) {
-        k_gexec<<<gp->grid, kGThreads, kGSmem, st>>>(a);
+        launch_gexec(gp, gp->grid, a, st);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;

@@ -44,6 +44,7 @@ struct GraphPlan {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphNode_t knode[2] = {nullptr, nullptr};
     bool use_graph = true;
+    bool mix = false;  // has compile-time mixed-radix stages: runs the executor built with them
     int64_t spin_limit = int64_t(1) << 23;
     std::string desc;
     int64_t* line_off = nullptr;              // grouped-line offsets (device)
