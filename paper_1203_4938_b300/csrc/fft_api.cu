@@ -517,16 +517,26 @@ fft_status build_mixed_1d(fft_plan_s* p, int m, int k) {
     return FFT_OK;
 }
 
-// N = M * 2^k > 4096 (M = 3, 5, 7): four-step N = N1 * N2 with N2 = 2^b,
-// b = min(12, k - 2) (at least 4 transposed rows per CTA), N1 = M * 2^(k - b)
-// columns by the compile-time mixed kernel, then the power-of-two
-// transposed rows.  Returns FFT_ERR_UNSUPPORTED where no column kernel fits.
+// N = M * 2^k > 4096 (M = 3, 5, 7): four-step N = N1 * N2 with N1 = M * 2^a
+// columns by the compile-time mixed kernel, then N2 = 2^b rows by the
+// power-of-two transposed-row kernel.  Measured on 2^24 elements per exec
+// (sweep over b = 7..12 and 4..32 rows per CTA): b = 8 with 16 rows per CTA
+// (128-byte store runs) from k = 12, N1 at most M * 2^6, then b grows to 12
+// with 8 (b <= 11) or 4 rows per CTA; k < 12: a = 2.  Against b = min(12, k-2)
+// with 4 rows: 49152 112.0 -> 103.9 us, 57344 109.2 -> 101.9 us.
+// Returns FFT_ERR_UNSUPPORTED where no column kernel fits.
 fft_status build_mixed_fourstep(fft_plan_s* p, int m, int k) {
-    const int b = k - 2 < 12 ? k - 2 : 12, a = k - b;
+    int a = k >= 12 ? k - 8 : 2;
+    if (a > 6) a = 6;
+    if (k - a > 12) a = k - 12;
+    int b = env_int("B300FFT_MIXED_B", k - a);
+    if (b < 6 || b > 12 || b > k) return FFT_ERR_UNSUPPORTED;
+    a = k - b;
     const int c = mixed_cols_width(m, a);
     if (b < 6 || c == 0 || c > (1 << b)) return FFT_ERR_UNSUPPORTED;
     const int64_t n1 = int64_t(m) << a, n2 = int64_t(1) << b, n = n1 * n2;
-    int tpc = 16;
+    int tpc = env_int("B300FFT_MIXED_TPC", b <= 8 ? 16 : (b <= 11 ? 8 : 4));
+    if (tpc < 2 || tpc > 64 || (tpc & (tpc - 1))) tpc = 16;
     while (tpc > 2 && (rowsT_threads(b, tpc) > 1024 || n1 % tpc != 0)) tpc /= 2;
     if (n1 % tpc != 0 || rowsT_threads(b, tpc) > 1024) return FFT_ERR_UNSUPPORTED;
     int lg = 0;
