@@ -41,10 +41,10 @@ METRIC = "C2C FFT GFLOP/s (5N*log2N/t), fwd+inv sweep N=2^10..2^24, 2^26 complex
 # --no-cpu` (mean of the forward and inverse launches).  The numbers belong to
 # the kernel sources hashed in TRAFFIC_SOURCES; when those files change the
 # benchmark reports the traffic as null until a new capture replaces them.
-MEASURED_DRAM_MB = {10: 1018, 11: 1020, 12: 1020, 13: 1022, 14: 1022, 15: 1356, 16: 1018, 17: 1422, 18: 1457, 19: 1023, 20: 1131, 21: 2152, 22: 2152, 23: 2018, 24: 2171}
+MEASURED_DRAM_MB = {10: 1018, 11: 1020, 12: 1020, 13: 1022, 14: 1021, 15: 1356, 16: 1017, 17: 1420, 18: 1457, 19: 1023, 20: 1125, 21: 1396, 22: 1356, 23: 2017, 24: 2167}
 TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threestep.cuh", "kernels_launch.cuh",
                    "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu", "fft_api.cu", "exec.cu"]
-TRAFFIC_SOURCES_SHA = "3eec3f8a2882f52b"
+TRAFFIC_SOURCES_SHA = "279f07e7311b32b2"
 
 
 def traffic_sources_sha() -> str:
