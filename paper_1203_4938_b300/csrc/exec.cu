@@ -132,6 +132,18 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                                 nullptr, nullptr, 0, st);
             break;
         }
+        case PlanKind::TwoDMixed: {
+            const int64_t h = p->len[0], w = p->len[1];
+            const float2* tb = p->d_tables + p->off_b;
+            if (want(0))
+                e = p->mix_mw ? launch_rows_mixed(p->mix_mw, p->logn_a, inv, in, out, p->batch * h, p->d_tables, st)
+                              : launch_rows(p->logn_a, inv, in, out, p->batch * h, p->d_tables, st);
+            if (e == cudaSuccess && want(1))
+                e = p->mix_mh ? launch_cols2d_mixed(p->mix_mh, p->logn_b, inv, out, out, w, p->batch, tb, st)
+                              : launch_cols(p->logn_b, p->cols_c, inv, false, out, out, w, w, h * w, p->batch, tb,
+                                            nullptr, nullptr, 0, st);
+            break;
+        }
         case PlanKind::Real:
             if (!want(0)) return FFT_OK;
             return exec_real(p, in, out, inv, st);

@@ -571,6 +571,49 @@ fft_status build_mixed_fourstep(fft_plan_s* p, int m, int k) {
     return FFT_OK;
 }
 
+// 2-D [H][W] where each side is a power of two (rows <= 2^14, columns
+// <= 2^12 points) or M * 2^K <= 4096 (M = 3, 5, 7) and at least one side is
+// the latter: the rows kernel of W, then the in-place column pass over H.
+fft_status build_mixed_2d(fft_plan_s* p, int64_t h, int64_t w) {
+    int mh = 0, kh = 0, mw = 0, kw = 0;
+    const int lh = ilog2_exact(h), lw = ilog2_exact(w);
+    const bool mix_h = lh < 0 && mixed_supported(h, &mh, &kh), mix_w = lw < 0 && mixed_supported(w, &mw, &kw);
+    if ((lh < 0 && !mix_h) || (lw < 0 && !mix_w)) return FFT_ERR_UNSUPPORTED;
+    if ((!mix_w && lw > kRowsMaxLog) || (!mix_h && (lh > kColsMaxLog || lh < 1))) return FFT_ERR_UNSUPPORTED;
+    int c = 0;
+    if (mix_h) {
+        c = mixed_cols2d_width(mh, kh);
+        if (c == 0 || w % c != 0) return FFT_ERR_UNSUPPORTED;
+    } else {
+        c = cols_width_for(lh, w);
+        if (c == 0) return FFT_ERR_UNSUPPORTED;
+    }
+    const int ea = mix_w ? mixed_table_entries(mw, kw) : pow2_table_entries(lw);
+    const int eb = mix_h ? mixed_table_entries(mh, kh) : pow2_table_entries(lh);
+    if (ea < 0 || eb < 0) return FFT_ERR_UNSUPPORTED;
+    p->off_a = 0;
+    p->off_b = (size_t)ea;
+    fft_status s = alloc_tables(p, (size_t)ea + (size_t)eb);
+    if (s != FFT_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (ea > 0) e = mix_w ? gen_mixed_table(p->d_tables, mw, kw, 0) : gen_pow2_table(p->d_tables, lw, 0);
+    if (e == cudaSuccess && eb > 0)
+        e = mix_h ? gen_mixed_table(p->d_tables + p->off_b, mh, kh, 0) : gen_pow2_table(p->d_tables + p->off_b, lh, 0);
+    if (e == cudaSuccess && !mix_w) e = rows_prepare(lw);
+    if (e == cudaSuccess && !mix_h) e = cols_prepare(lh, c);
+    if (e != cudaSuccess) return FFT_ERR_CUDA;
+    p->kind = PlanKind::TwoDMixed;
+    p->mix_mw = mix_w ? mw : 0;
+    p->mix_mh = mix_h ? mh : 0;
+    p->logn_a = mix_w ? kw : lw;
+    p->logn_b = mix_h ? kh : lh;
+    p->cols_c = c;
+    p->kernels = 2;
+    std::snprintf(p->desc, sizeof p->desc, "2d-mixed H=%lld W=%lld: rows (%s) then cols (%s, %d per CTA)",
+                  (long long)h, (long long)w, mix_w ? "mixed" : "power of two", mix_h ? "mixed" : "power of two", c);
+    return FFT_OK;
+}
+
 // Non-power-of-two 1-D lengths: mixed radix 2/3/4/5/7/8/16 (single tile or
 // four-step) or Bluestein, through the stage-graph executor.
 fft_status build_generic_1d(fft_plan_s* p) {
@@ -641,6 +684,7 @@ fft_plan fft_plan_create(int dims, const int64_t* lengths, int64_t batch, int pr
     } else {
         const int lh = ilog2_exact(lengths[0]), lw = ilog2_exact(lengths[1]);
         if (lh >= 0 && lw >= 0) s = build_pow2_2d(p, lh, lw);
+        else if (env_int("B300FFT_MIXED", 1) != 0) s = build_mixed_2d(p, lengths[0], lengths[1]);
         else s = FFT_ERR_UNSUPPORTED;
     }
     if (s != FFT_OK) return fail(s, p);

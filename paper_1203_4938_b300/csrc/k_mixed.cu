@@ -54,6 +54,42 @@ cudaError_t launch_cols_mixed(int m, int a, bool inv, const float2* in, float2* 
     return cudaErrorInvalidValue;
 }
 
+// Column pass of a 2-D transform with a side of M * 2^K: NL = min(32, the
+// largest power of two <= 4096 / L) adjacent columns per CTA.
+#define B300_MIXED_COLS2D(X)                                                                                  \
+    X(3, 0, 32) X(3, 1, 32) X(3, 2, 32) X(3, 3, 32) X(3, 4, 32) X(3, 5, 32) X(3, 6, 16) X(3, 7, 8) X(3, 8, 4)   \
+    X(3, 9, 2) X(3, 10, 1) X(5, 0, 32) X(5, 1, 32) X(5, 2, 32) X(5, 3, 32) X(5, 4, 32) X(5, 5, 16) X(5, 6, 8)   \
+    X(5, 7, 4) X(5, 8, 2) X(5, 9, 1) X(7, 0, 32) X(7, 1, 32) X(7, 2, 32) X(7, 3, 32) X(7, 4, 32) X(7, 5, 16)    \
+    X(7, 6, 8) X(7, 7, 4) X(7, 8, 2) X(7, 9, 1)
+
+int mixed_cols2d_width(int m, int k) {
+#define B300_X(M, K, NL) \
+    if (m == M && k == K) return NL;
+    B300_MIXED_COLS2D(B300_X)
+#undef B300_X
+    return 0;
+}
+
+cudaError_t launch_cols2d_mixed(int m, int k, bool inv, const float2* in, float2* out, int64_t S2, int64_t items,
+                                const float2* tw, cudaStream_t st) {
+#define B300_X(M, K, NL)                                                                                        \
+    if (m == M && k == K) {                                                                                     \
+        if (S2 % NL != 0 || items <= 0) return cudaErrorInvalidValue;                                         \
+        const int64_t g = items * (S2 / NL);                                                                    \
+        if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;                                            \
+        if (inv)                                                                                                \
+            k_cols_mixed<M, K, NL, true, false><<<(unsigned)g, 256, 0, st>>>(in, out, S2, items, tw, nullptr,   \
+                                                                               nullptr, 0);                     \
+        else                                                                                                    \
+            k_cols_mixed<M, K, NL, false, false><<<(unsigned)g, 256, 0, st>>>(in, out, S2, items, tw, nullptr,  \
+                                                                                nullptr, 0);                    \
+        return cudaGetLastError();                                                                              \
+    }
+    B300_MIXED_COLS2D(B300_X)
+#undef B300_X
+    return cudaErrorInvalidValue;
+}
+
 namespace {
 template <int M, int K>
 cudaError_t one(int op, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw, cudaStream_t st,

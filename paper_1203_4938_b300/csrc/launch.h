@@ -42,6 +42,11 @@ cudaError_t launch_rows_mixed(int m, int k, bool inv, const float2* in, float2* 
 // `items` row-major [M * 2^a][S2] arrays, mixed_cols_width(m, a) columns per
 // CTA (0: no kernel for that length), times W_N^{n2 k1} from (lo, hi, sh).
 int mixed_cols_width(int m, int a);
+// 2-D column pass: columns of length M * 2^K (no twiddle), mixed_cols2d_width
+// columns per CTA (S2 must be a multiple of it).
+int mixed_cols2d_width(int m, int k);
+cudaError_t launch_cols2d_mixed(int m, int k, bool inv, const float2* in, float2* out, int64_t S2, int64_t items,
+                                const float2* tw, cudaStream_t st);
 cudaError_t launch_cols_mixed(int m, int a, bool inv, const float2* in, float2* out, int64_t S2, int64_t items,
                               const float2* tw, const float2* lo, const float2* hi, int sh, cudaStream_t st);
 

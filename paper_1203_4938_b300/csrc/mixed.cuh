@@ -102,9 +102,10 @@ struct MixRows {
 };
 
 // Adjacent columns of a row-major [L][S2] array (in / out at the tile's first
-// column col0); stored values times W_N^{(col0 + line) e} from the two-level
-// table W(m) = hi[m >> sh] * lo[m mod 2^sh].
-template <bool INV>
+// column col0).  TW: stored values times W_N^{(col0 + line) e} from the
+// two-level table W(m) = hi[m >> sh] * lo[m mod 2^sh] (four-step first pass,
+// into the workspace); otherwise plain final stores (2-D column pass).
+template <bool INV, bool TW = true>
 struct MixCols {
     static constexpr bool LINE_FAST = true;
     const float2* in;
@@ -116,8 +117,12 @@ struct MixCols {
     int sh;
     __device__ __forceinline__ float2 load(int line, int e) const { return __ldcs(in + e * S2 + line); }
     __device__ __forceinline__ void store(int line, int e, float2 v) const {
-        v = twmul<INV>(v, root2(lo, hi, (col0 + (uint32_t)line) * (uint32_t)e, sh));
-        __stcg(out + e * S2 + line, v);
+        if constexpr (TW) {
+            v = twmul<INV>(v, root2(lo, hi, (col0 + (uint32_t)line) * (uint32_t)e, sh));
+            __stcg(out + e * S2 + line, v);
+        } else {
+            __stcs(out + e * S2 + line, v);
+        }
     }
 };
 
@@ -198,10 +203,12 @@ __global__ void __launch_bounds__(256, 3) k_rows_mixed(const float2* __restrict_
     mix_pass<MP, 0, INV>(io, smem, nl, tw);
 }
 
-// Four-step first pass of N = L * S2 (L = M * 2^K): for each of `items`
-// row-major [L][S2] arrays, columns of length L, NL adjacent columns per
-// CTA (S2 % NL == 0), into `out` (same layout) times W_N^{n2 k1}.
-template <int M, int K, int NL, bool INV>
+// Column transforms of length L = M * 2^K over `items` row-major [L][S2]
+// arrays, NL adjacent columns per CTA (S2 % NL == 0), into `out` (same layout;
+// out == in allowed: a tile reads its columns before its first store).  TW:
+// the four-step first pass of N = L * S2, times W_N^{n2 k1}; otherwise the
+// column pass of a 2-D transform.
+template <int M, int K, int NL, bool INV, bool TW = true>
 __global__ void __launch_bounds__(256, 3) k_cols_mixed(const float2* __restrict__ in, float2* __restrict__ out,
                                                        int64_t S2, int64_t items, const float2* __restrict__ tw,
                                                        const float2* __restrict__ lo, const float2* __restrict__ hi,
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(256, 3) k_cols_mixed(const float2* __restrict_
     const int64_t item = (int64_t)blockIdx.x / tiles_per_item;
     const int64_t col0 = ((int64_t)blockIdx.x - item * tiles_per_item) * NL;
     const int64_t base = item * MP::L * S2 + col0;
-    const MixCols<INV> io{in + base, out + base, S2, (uint32_t)col0, lo, hi, sh};
+    const MixCols<INV, TW> io{in + base, out + base, S2, (uint32_t)col0, lo, hi, sh};
     mix_pass<MP, 0, INV>(io, smem, NL, tw);
 }
 

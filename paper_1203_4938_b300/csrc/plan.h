@@ -20,6 +20,7 @@ enum class PlanKind : int {
     TwoDPersist,  // both 2-D passes in one persistent launch, L2-resident chunks of images
     RowsMixed, // single-pass mixed-radix rows kernel, L = M * 2^K <= 4096 (M = 3, 5, 7)
     FourStepMixed, // N = (M * 2^a) * 2^b: mixed columns kernel + power-of-two transposed rows
+    TwoDMixed, // 2-D with a side of M * 2^K: rows kernel (power of two or mixed), then in-place column pass
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
     Ragged,    // persistent work-queue kernel over uneven lengths
@@ -45,6 +46,7 @@ struct fft_plan_s {
     // power-of-two kernels
     int logn_a = 0, logn_b = 0, sh = 0;
     int mix_m = 0;  // RowsMixed: L = mix_m * 2^logn_a
+    int mix_mh = 0, mix_mw = 0;  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
     int cols_c = 0;     // columns kernel width
     int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA
 

@@ -110,3 +110,31 @@ def test_beyond_column_kernels_falls_back(torch, n):
     x = inputs.normal_batch(1, n, seed=3)
     y = run((n,), 1, x, -1)
     assert max_rel_l2(y, oracle.fft(x, -1), -1) <= TOL_FP32
+
+
+@pytest.mark.parametrize("h,w,batch", [(768, 1024, 2), (1024, 768, 2), (96, 160, 5), (3, 64, 7), (5, 7 * 32, 3),
+                                       (3072, 512, 1), (448, 3584, 1), (2048, 5 * 128, 1), (4096, 3072, 1)])
+def test_2d_with_mixed_sides(torch, h, w, batch):
+    rng = np.random.default_rng(h * 7 + w)
+    x = (rng.standard_normal((batch, h, w)) + 1j * rng.standard_normal((batch, h, w))).astype(np.complex64)
+    with F.Plan((h, w), batch) as p:
+        assert p.describe().startswith("2d-mixed"), p.describe()
+    for d in (-1, +1):
+        y = run((h, w), batch, x, d)
+        assert max_rel_l2(y.reshape(batch, -1), oracle.fft2(x, d).reshape(batch, -1), -1) <= TOL_FP32, (h, w, d)
+
+
+def test_2d_mixed_in_place(torch):
+    h, w, batch = 320, 96, 3
+    x = inputs.uniform_batch(batch * h, w, seed=9).reshape(batch, h, w)
+    for d in (-1, +1):
+        y = run((h, w), batch, x, d, inplace=True)
+        assert max_rel_l2(y.reshape(batch, -1), oracle.fft2(x, d).reshape(batch, -1), -1) <= TOL_FP32, d
+
+
+@pytest.mark.parametrize("h,w", [(7, 5), (9, 64), (64, 11)])
+def test_2d_unsupported_sides(torch, h, w):
+    # 7 x 5: a 7-point column tile holds 32 columns and 5 is not a multiple;
+    # 9 and 11 are not M * 2^K: no 2-D plan, FFT_ERR_UNSUPPORTED
+    assert F.fft_plan_create(2, [h, w], 1, 0) is None
+    assert F.fft_last_error() == F.FFT_ERR_UNSUPPORTED
