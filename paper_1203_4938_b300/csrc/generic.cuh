@@ -85,7 +85,8 @@ struct GExecArgs {
     const GTransform* xf;
     const uint64_t* items;  // (transform << 32) | (stage << 24) | tile
     int nitems;
-    int* ctl;  // [0] queue head, [1 + c] dependency counters
+    int* ctl;    // [0] queue head, [1 + c] dependency counters
+    int* qhead;  // queue head of this launch (ctl[0], or a second head past the counters)
     int* status;
     int64_t spin_limit;
     int single;  // per-stage launch: item = item0 + blockIdx.x, no waits
@@ -446,8 +447,9 @@ __device__ __forceinline__ void g_pow2_tile(const GExecArgs& a, const GTransform
     }
 }
 
-// Run queue item p (tile of one stage of one transform).
-template <bool MIX>
+// Run queue item p (tile of one stage of one transform).  LEAN: the plan has
+// templated power-of-two stages only (no runtime tile is compiled in).
+template <bool MIX, bool LEAN>
 __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* smem, int* s_ok) {
     const uint64_t it = a.items[p];
     const int t = (int)(it >> 32);
@@ -474,9 +476,9 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
         __syncthreads();
         if (!*s_ok) return;
     }
-    if (st.tmpl) {
+    if (LEAN || st.tmpl) {
         g_pow2_tile<MIX>(a, x, st, tile, smem);
-    } else {
+    } else if constexpr (!LEAN) {
         const int line0 = tile * st.lpt;
         const int nl = min(st.lpt, st.nlines - line0);
         const float2* gin = g_buf_in(a, x, st.in_buf);
@@ -493,26 +495,32 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
     }
 }
 
+// Shared memory of the templated power-of-two tiles (the lean executor's buffer).
+constexpr int cmax(int x, int y) { return x > y ? x : y; }
+constexpr int kGSmemLean =
+    cmax(cmax(cmax(ColsCfg<6, 64>::SMEM, ColsCfg<7, 32>::SMEM), cmax(ColsCfg<8, 16>::SMEM, RowsTCfg<7, 32>::SMEM)),
+         RowsTCfg<8, 16>::SMEM);
+
 // Persistent executor (single = 0) or one launch per stage group (single = 1:
 // block b runs item item0 + b; the stream orders the stages).  MIX: the plan
 // has compile-time mixed-radix stages (a separate kernel, so plans without
 // them keep the smaller kernel's register allocation).
-template <bool MIX>
-__global__ void __launch_bounds__(kGThreads, 3) k_gexec(GExecArgs a) {
+template <bool MIX, bool LEAN>
+__global__ void __launch_bounds__(kGThreads, LEAN ? 4 : 3) k_gexec(GExecArgs a) {
     extern __shared__ float2 smem[];
     __shared__ int s_item[2];
     __shared__ int s_ok;
     if (a.single) {
-        g_run_item<MIX>(a, a.item0 + blockIdx.x, smem, &s_ok);
+        g_run_item<MIX, LEAN>(a, a.item0 + blockIdx.x, smem, &s_ok);
         return;
     }
-    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl, 1);
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.qhead, 1);
     for (int it = 0;; it ^= 1) {
         __syncthreads();
         const int p = s_item[it];
         if (p >= a.nitems) break;
-        if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.ctl, 1);
-        g_run_item<MIX>(a, p, smem, &s_ok);
+        if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.qhead, 1);
+        g_run_item<MIX, LEAN>(a, p, smem, &s_ok);
     }
 }
 

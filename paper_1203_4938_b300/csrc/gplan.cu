@@ -24,13 +24,33 @@ int env_i(const char* name, int dflt) {
     return (v && *v) ? std::atoi(v) : dflt;
 }
 
-// The executor kernel a plan runs (with or without the compile-time mixed tiles).
-const void* gexec_fn(const GraphPlan* gp) {
-    return gp->mix ? (const void*)k_gexec<true> : (const void*)k_gexec<false>;
+// The executor kernels: with the compile-time mixed tiles, lean (templated
+// power-of-two stages only: 4 CTAs per SM), or the base one.
+enum GKind : int { GK_BASE = 0, GK_MIX = 1, GK_LEAN = 2 };
+const void* gexec_fn(int k) {
+    return k == GK_MIX ? (const void*)k_gexec<true, false>
+                       : (k == GK_LEAN ? (const void*)k_gexec<false, true> : (const void*)k_gexec<false, false>);
 }
-void launch_gexec(const GraphPlan* gp, int grid, const GExecArgs& a, cudaStream_t st) {
-    if (gp->mix) k_gexec<true><<<grid, kGThreads, kGSmem, st>>>(a);
-    else k_gexec<false><<<grid, kGThreads, kGSmem, st>>>(a);
+int gexec_smem(int k) { return k == GK_LEAN ? kGSmemLean : kGSmem; }
+void launch_gexec(int k, int grid, const GExecArgs& a, cudaStream_t st) {
+    if (k == GK_MIX) k_gexec<true, false><<<grid, kGThreads, kGSmem, st>>>(a);
+    else if (k == GK_LEAN) k_gexec<false, true><<<grid, kGThreads, kGSmemLean, st>>>(a);
+    else k_gexec<false, false><<<grid, kGThreads, kGSmem, st>>>(a);
+}
+int plan_kind(const GraphPlan* gp) { return gp->mix ? GK_MIX : (gp->lean ? GK_LEAN : GK_BASE); }
+
+// The persistent launches of a plan (see GraphPlan::nrest).
+struct GPart {
+    int kind, item0, nitems, grid, head;
+};
+int gexec_parts(const GraphPlan* gp, GPart* parts) {
+    if (gp->nrest > 0 && gp->nrest < gp->nitems) {
+        parts[0] = {gp->mix ? GK_MIX : GK_BASE, 0, gp->nrest, gp->grid, 0};
+        parts[1] = {GK_LEAN, gp->nrest, gp->nitems - gp->nrest, gp->grid_lean, 1 + gp->ncounters};
+        return 2;
+    }
+    parts[0] = {plan_kind(gp), 0, gp->nitems, gp->grid, 0};
+    return 1;
 }
 
 bool is_smooth(int64_t n) {
@@ -438,6 +458,7 @@ GExecArgs make_args(const GraphPlan* gp, const float2* in, float2* out, bool inv
     a.items = single ? gp->items : gp->items_lag;
     a.nitems = gp->nitems;
     a.ctl = gp->ctl;
+    a.qhead = gp->ctl;
     a.status = d_status;
     a.spin_limit = gp->spin_limit;
     a.single = single;
@@ -767,6 +788,36 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
                 items_lag.push_back(((uint64_t)g.t << 32) | ((uint64_t)g.s << 24) | (uint64_t)tile);
         if (items_lag.size() != items.size()) return FFT_ERR_UNSUPPORTED;
     }
+    // transforms whose stages are all templated power-of-two tiles run in the
+    // lean executor; with other transforms present they go last, in a launch
+    // of their own (queue order kept within each part)
+    gp->mix = false;
+    gp->lean = env_i("B300FFT_G_LEAN", 1) != 0;
+    gp->nrest = 0;
+    {
+        std::vector<char> xlean(xf.size(), 1);
+        bool any_lean = false, all_lean = true;
+        for (size_t t = 0; t < xf.size(); ++t) {
+            for (int s2 = 0; s2 < xf[t].nstages; ++s2) {
+                const int tm = B.st_f[xf[t].kind + s2].tmpl;
+                xlean[t] &= tm > 0 && tm < 1000;
+                gp->mix = gp->mix || tm >= 1000;
+            }
+            any_lean = any_lean || xlean[t];
+            all_lean = all_lean && xlean[t];
+        }
+        if (!gp->lean) {
+            any_lean = all_lean = false;
+        }
+        gp->lean = all_lean;
+        if (any_lean && !all_lean && env_i("B300FFT_G_SPLIT", 1) != 0) {
+            std::vector<uint64_t> rest, lean;
+            for (uint64_t it : items_lag) (xlean[it >> 32] ? lean : rest).push_back(it);
+            gp->nrest = (int)rest.size();
+            rest.insert(rest.end(), lean.begin(), lean.end());
+            items_lag.swap(rest);
+        }
+    }
 
     // device data
     cudaStream_t st = 0;
@@ -807,26 +858,35 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
     gp->nitems = (int)items.size();
     gp->ncounters = ctr;
     gp->ntransforms = (int)xf.size();
-    if (cudaMalloc(&gp->ctl, sizeof(int) * (size_t)(1 + ctr)) != cudaSuccess) return FFT_ERR_ALLOC;
+    if (cudaMalloc(&gp->ctl, sizeof(int) * (size_t)(2 + ctr)) != cudaSuccess) return FFT_ERR_ALLOC;
     gp->work_bytes = (size_t)woff * sizeof(float2);
     if (woff > 0 && cudaMalloc(&gp->work, gp->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
-    gp->mix = false;
-    for (const GStage& g : B.st_f) gp->mix = gp->mix || g.tmpl >= 1000;
-    const void* kfn = gexec_fn(gp);
-    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem) != cudaSuccess)
-        return FFT_ERR_CUDA;
-    int bps = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, kGThreads, kGSmem) != cudaSuccess || bps < 1)
-        return FFT_ERR_CUDA;
+    int bps[3] = {0, 0, 0}, dev = 0, sms = 0;
+    for (int k = 0; k < 3; ++k) {
+        const void* kfn = gexec_fn(k);
+        if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, gexec_smem(k)) != cudaSuccess)
+            return FFT_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[k], kfn, kGThreads, gexec_smem(k)) != cudaSuccess ||
+            bps[k] < 1)
+            return FFT_ERR_CUDA;
+    }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    gp->grid = std::max(1, std::min(gp->nitems, sms * bps));
+    {
+        GPart parts[2];
+        gp->grid = gp->nitems;  // placeholders for gexec_parts
+        const int np = gexec_parts(gp, parts);
+        gp->grid = std::max(1, std::min(parts[0].nitems, sms * bps[parts[0].kind]));
+        gp->grid_lean = np > 1 ? std::max(1, std::min(parts[1].nitems, sms * bps[GK_LEAN])) : 0;
+    }
     gp->spin_limit = env_i("B300FFT_SPIN_LIMIT", 1 << 23);
     gp->use_graph = env_i("B300FFT_GRAPH", 1) != 0;
     char buf[256];
-    std::snprintf(buf, sizeof buf, "graph kinds=%zu transforms=%d items=%d stages<=%d grid=%d work=%zuB pool=%lldB",
-                  uniq.size(), gp->ntransforms, gp->nitems, maxst, gp->grid, gp->work_bytes,
-                  (long long)(B.pool_size * 8));
+    std::snprintf(buf, sizeof buf,
+                  "graph kinds=%zu transforms=%d items=%d stages<=%d grid=%d%s work=%zuB pool=%lldB",
+                  uniq.size(), gp->ntransforms, gp->nitems, maxst, gp->grid,
+                  gp->lean ? " lean" : (gp->nrest > 0 && gp->nrest < gp->nitems ? " +lean launch" : ""),
+                  gp->work_bytes, (long long)(B.pool_size * 8));
     gp->desc = buf;
     if (cudaDeviceSynchronize() != cudaSuccess) return FFT_ERR_CUDA;
     return FFT_OK;
@@ -861,18 +921,26 @@ void graph_plan_free(GraphPlan* gp) {
 }
 
 namespace {
-// Capture memset(ctl) + the persistent launch once per direction; later
-// execs only patch the in/out pointers of the kernel node.
+// Capture memset(ctl) + the persistent launch(es) once per direction; later
+// execs only patch the arguments of the kernel nodes.
 cudaError_t ensure_graph(GraphPlan* gp, bool inv, const GExecArgs& a) {
     const int d = inv ? 1 : 0;
     if (gp->gexec[d]) return cudaSuccess;
+    GPart parts[2];
+    const int np = gexec_parts(gp, parts);
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(1 + gp->ncounters), cs);
-        launch_gexec(gp, gp->grid, a, cs);
+        cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(2 + gp->ncounters), cs);
+        for (int i = 0; i < np; ++i) {
+            GExecArgs b = a;
+            b.items += parts[i].item0;
+            b.nitems = parts[i].nitems;
+            b.qhead = gp->ctl + parts[i].head;
+            launch_gexec(parts[i].kind, parts[i].grid, b, cs);
+        }
         e = cudaStreamEndCapture(cs, &gp->graph[d]);
     }
     cudaStreamDestroy(cs);
@@ -884,9 +952,14 @@ cudaError_t ensure_graph(GraphPlan* gp, bool inv, const GExecArgs& a) {
     for (auto n : nodes) {
         cudaGraphNodeType t;
         cudaGraphNodeGetType(n, &t);
-        if (t == cudaGraphNodeTypeKernel) gp->knode[d] = n;
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(n, &kp) != cudaSuccess) return cudaErrorUnknown;
+        for (int i = 0; i < np; ++i)
+            if (kp.func == gexec_fn(parts[i].kind)) gp->knode[d][i] = n;
     }
-    if (!gp->knode[d]) return cudaErrorUnknown;
+    for (int i = 0; i < np; ++i)
+        if (!gp->knode[d][i]) return cudaErrorUnknown;
     return cudaGraphInstantiate(&gp->gexec[d], gp->graph[d], 0);
 }
 }  // namespace
@@ -895,34 +968,46 @@ fft_status graph_plan_exec(GraphPlan* gp, const float2* in, float2* out, bool in
                            bool per_stage) {
     cudaError_t e = cudaSuccess;
     if (per_stage) {
+        const int k = gp->mix ? GK_MIX : (gp->lean ? GK_LEAN : GK_BASE);
         for (auto& g : gp->groups) {
             GExecArgs a = make_args(gp, in, out, inv, d_status, 1, g.first);
-            launch_gexec(gp, g.second - g.first, a, st);
+            launch_gexec(k, g.second - g.first, a, st);  // a split plan is not lean: the full executor
             e = cudaGetLastError();
             if (e != cudaSuccess) return FFT_ERR_CUDA;
         }
         return FFT_OK;
     }
     GExecArgs a = make_args(gp, in, out, inv, d_status, 0, 0);
+    GPart parts[2];
+    const int np = gexec_parts(gp, parts);
+    GExecArgs pa[2];
+    for (int i = 0; i < np; ++i) {
+        pa[i] = a;
+        pa[i].items += parts[i].item0;
+        pa[i].nitems = parts[i].nitems;
+        pa[i].qhead = gp->ctl + parts[i].head;
+    }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
     if (gp->use_graph && cap == cudaStreamCaptureStatusNone) {
         const int d = inv ? 1 : 0;
         if (ensure_graph(gp, inv, a) != cudaSuccess) return FFT_ERR_CUDA;
-        cudaKernelNodeParams kp{};
-        void* params[1] = {&a};
-        kp.func = const_cast<void*>(gexec_fn(gp));
-        kp.gridDim = dim3(gp->grid);
-        kp.blockDim = dim3(kGThreads);
-        kp.sharedMemBytes = kGSmem;
-        kp.kernelParams = params;
-        e = cudaGraphExecKernelNodeSetParams(gp->gexec[d], gp->knode[d], &kp);
+        for (int i = 0; i < np && e == cudaSuccess; ++i) {
+            cudaKernelNodeParams kp{};
+            void* params[1] = {&pa[i]};
+            kp.func = const_cast<void*>(gexec_fn(parts[i].kind));
+            kp.gridDim = dim3(parts[i].grid);
+            kp.blockDim = dim3(kGThreads);
+            kp.sharedMemBytes = gexec_smem(parts[i].kind);
+            kp.kernelParams = params;
+            e = cudaGraphExecKernelNodeSetParams(gp->gexec[d], gp->knode[d][i], &kp);
+        }
         if (e == cudaSuccess) e = cudaGraphLaunch(gp->gexec[d], st);
         return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;
     }
-    e = cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(1 + gp->ncounters), st);
-    if (e == cudaSuccess) {
-        launch_gexec(gp, gp->grid, a, st);
+    e = cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(2 + gp->ncounters), st);
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+        launch_gexec(parts[i].kind, parts[i].grid, pa[i], st);
         e = cudaGetLastError();
     }
     return e == cudaSuccess ? FFT_OK : FFT_ERR_CUDA;

@@ -42,9 +42,14 @@ struct GraphPlan {
     // graphs of the persistent launch, one per direction
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    cudaGraphNode_t knode[2] = {nullptr, nullptr};
+    cudaGraphNode_t knode[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [direction][launch]
     bool use_graph = true;
-    bool mix = false;  // has compile-time mixed-radix stages: runs the executor built with them
+    bool mix = false;   // has compile-time mixed-radix stages: runs the executor built with them
+    bool lean = false;  // templated power-of-two stages only: runs the lean executor (4 CTAs per SM)
+    // Plans where only some transforms qualify for the lean executor run two
+    // persistent launches: the first nrest queue items (the other transforms)
+    // in the full executor, then the rest in the lean one (grid_lean CTAs).
+    int nrest = 0, grid_lean = 0;
     int64_t spin_limit = int64_t(1) << 23;
     std::string desc;
     int64_t* line_off = nullptr;              // grouped-line offsets (device)

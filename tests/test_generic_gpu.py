@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_1203_4938_b300 import fft as F
 from paper_1203_4938_b300 import inputs
 from tests.gpu_util import TOL_FP32, cuda_or_skip, max_rel_l2, run, to_dev
 
@@ -100,19 +101,39 @@ def test_ragged_small_mix(torch, per_size):
         assert _ragged_check(torch, lengths, data, per_size, d) <= TOL_FP32
 
 
-@pytest.mark.parametrize("env", [{}, {"B300FFT_G_POW2T": "0"}, {"B300FFT_G_LAG": "1"}, {"B300FFT_G_LAG": "100000"}])
+@pytest.mark.parametrize("env", [{}, {"B300FFT_G_POW2T": "0"}, {"B300FFT_G_LAG": "1"}, {"B300FFT_G_LAG": "100000"},
+                                 {"B300FFT_G_SPLIT": "0"}, {"B300FFT_G_LEAN": "0"}, {"B300FFT_GRAPH": "0"},
+                                 {"B300FFT_G_MIXT": "0"}])
 def test_ragged_pow2_templated_stages(torch, monkeypatch, env):
     """Power-of-two lengths 2^13..2^16 inside a ragged batch run as templated
-    four-step stages (or, with B300FFT_G_POW2T=0, as runtime-radix stages);
-    the persistent queue lags each transform's second stage (B300FFT_G_LAG
-    items, 1 = right behind).  Every transform is compared in full."""
+    four-step stages (or, with B300FFT_G_POW2T=0, as runtime-radix stages) in
+    a launch of the lean executor after the other transforms (B300FFT_G_SPLIT=0
+    or B300FFT_G_LEAN=0: one launch of the full executor); the persistent
+    queue lags each transform's second stage (B300FFT_G_LAG items, 1 = right
+    behind).  Every transform is compared in full."""
     for k, v in env.items():
         monkeypatch.setenv(k, v)
-    lengths = [8192, 16384, 32768, 65536, 3 * 2 ** 13, 8192, 65536, 100, 4096, 16384, 2 ** 13, 7 * 2 ** 12]
+    lengths = [8192, 16384, 32768, 65536, 3 * 2 ** 13, 8192, 65536, 100, 4096, 16384, 2 ** 13, 7 * 2 ** 12, 1009]
     data = np.random.default_rng(21).standard_normal(2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    with F.Ragged(lengths) as p:
+        split = env.get("B300FFT_G_SPLIT", "1") != "0" and env.get("B300FFT_G_LEAN", "1") != "0" and \
+            env.get("B300FFT_G_POW2T", "1") != "0"
+        assert ("+lean launch" in p.describe()) == split, p.describe()
     for per_size in (False, True):
         for d in (-1, +1):
             assert _ragged_check(torch, lengths, data, per_size, d, full_limit=70000) <= TOL_FP32, (env, per_size, d)
+
+
+def test_ragged_all_lean(torch, monkeypatch):
+    """A ragged batch of power-of-two lengths 2^13..2^16 only runs in the lean
+    executor alone (one launch)."""
+    lengths = [8192, 65536, 16384, 32768, 8192, 65536, 16384]
+    data = np.random.default_rng(22).standard_normal(2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    with F.Ragged(lengths) as p:
+        assert " lean " in p.describe(), p.describe()
+    for per_size in (False, True):
+        for d in (-1, +1):
+            assert _ragged_check(torch, lengths, data, per_size, d, full_limit=70000) <= TOL_FP32, (per_size, d)
 
 
 def test_ragged_edge_lengths(torch):
