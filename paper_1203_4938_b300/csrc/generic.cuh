@@ -501,6 +501,9 @@ constexpr int kGSmemLean =
     cmax(cmax(cmax(ColsCfg<6, 64>::SMEM, ColsCfg<7, 32>::SMEM), cmax(ColsCfg<8, 16>::SMEM, RowsTCfg<7, 32>::SMEM)),
          RowsTCfg<8, 16>::SMEM);
 
+// The lean executor with the compile-time mixed tiles: their buffer and line offsets.
+constexpr int kGSmemLeanMix = cmax(kGSmemLean, kGMixOffF2 * 8 + kGMaxLines * 8);
+
 // Persistent executor (single = 0) or one launch per stage group (single = 1:
 // block b runs item item0 + b; the stream orders the stages).  MIX: the plan
 // has compile-time mixed-radix stages (a separate kernel, so plans without

@@ -24,20 +24,27 @@ int env_i(const char* name, int dflt) {
     return (v && *v) ? std::atoi(v) : dflt;
 }
 
-// The executor kernels: with the compile-time mixed tiles, lean (templated
-// power-of-two stages only: 4 CTAs per SM), or the base one.
-enum GKind : int { GK_BASE = 0, GK_MIX = 1, GK_LEAN = 2 };
+// The executor instantiations: full or lean (no runtime tiles, 4 CTAs per
+// SM), each with or without the compile-time mixed tiles.
+enum GKind : int { GK_BASE = 0, GK_MIX = 1, GK_LEAN = 2, GK_LEANMIX = 3 };
 const void* gexec_fn(int k) {
-    return k == GK_MIX ? (const void*)k_gexec<true, false>
-                       : (k == GK_LEAN ? (const void*)k_gexec<false, true> : (const void*)k_gexec<false, false>);
+    switch (k) {
+        case GK_MIX: return (const void*)k_gexec<true, false>;
+        case GK_LEAN: return (const void*)k_gexec<false, true>;
+        case GK_LEANMIX: return (const void*)k_gexec<true, true>;
+        default: return (const void*)k_gexec<false, false>;
+    }
 }
-int gexec_smem(int k) { return k == GK_LEAN ? kGSmemLean : kGSmem; }
+int gexec_smem(int k) { return k == GK_LEAN ? kGSmemLean : (k == GK_LEANMIX ? kGSmemLeanMix : kGSmem); }
 void launch_gexec(int k, int grid, const GExecArgs& a, cudaStream_t st) {
-    if (k == GK_MIX) k_gexec<true, false><<<grid, kGThreads, kGSmem, st>>>(a);
-    else if (k == GK_LEAN) k_gexec<false, true><<<grid, kGThreads, kGSmemLean, st>>>(a);
-    else k_gexec<false, false><<<grid, kGThreads, kGSmem, st>>>(a);
+    const int sm = gexec_smem(k);
+    switch (k) {
+        case GK_MIX: k_gexec<true, false><<<grid, kGThreads, sm, st>>>(a); break;
+        case GK_LEAN: k_gexec<false, true><<<grid, kGThreads, sm, st>>>(a); break;
+        case GK_LEANMIX: k_gexec<true, true><<<grid, kGThreads, sm, st>>>(a); break;
+        default: k_gexec<false, false><<<grid, kGThreads, sm, st>>>(a); break;
+    }
 }
-int plan_kind(const GraphPlan* gp) { return gp->mix ? GK_MIX : (gp->lean ? GK_LEAN : GK_BASE); }
 
 // The persistent launches of a plan (see GraphPlan::nrest).
 struct GPart {
@@ -45,11 +52,11 @@ struct GPart {
 };
 int gexec_parts(const GraphPlan* gp, GPart* parts) {
     if (gp->nrest > 0 && gp->nrest < gp->nitems) {
-        parts[0] = {gp->mix ? GK_MIX : GK_BASE, 0, gp->nrest, gp->grid, 0};
-        parts[1] = {GK_LEAN, gp->nrest, gp->nitems - gp->nrest, gp->grid_lean, 1 + gp->ncounters};
+        parts[0] = {gp->kfull, 0, gp->nrest, gp->grid, 0};
+        parts[1] = {gp->klean, gp->nrest, gp->nitems - gp->nrest, gp->grid_lean, 1 + gp->ncounters};
         return 2;
     }
-    parts[0] = {plan_kind(gp), 0, gp->nitems, gp->grid, 0};
+    parts[0] = {gp->lean ? gp->klean : gp->kfull, 0, gp->nitems, gp->grid, 0};
     return 1;
 }
 
@@ -788,29 +795,33 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
                 items_lag.push_back(((uint64_t)g.t << 32) | ((uint64_t)g.s << 24) | (uint64_t)tile);
         if (items_lag.size() != items.size()) return FFT_ERR_UNSUPPORTED;
     }
-    // transforms whose stages are all templated power-of-two tiles run in the
-    // lean executor; with other transforms present they go last, in a launch
-    // of their own (queue order kept within each part)
+    // transforms whose stages are all compile-time tiles run in the lean
+    // executor; with other transforms present they go last, in a launch of
+    // their own (queue order kept within each part)
     gp->mix = false;
-    gp->lean = env_i("B300FFT_G_LEAN", 1) != 0;
     gp->nrest = 0;
     {
+        const bool allow = env_i("B300FFT_G_LEAN", 1) != 0;
         std::vector<char> xlean(xf.size(), 1);
-        bool any_lean = false, all_lean = true;
+        bool any_lean = false, all_lean = true, mix_full = false, mix_lean = false;
         for (size_t t = 0; t < xf.size(); ++t) {
+            bool mx = false;
             for (int s2 = 0; s2 < xf[t].nstages; ++s2) {
                 const int tm = B.st_f[xf[t].kind + s2].tmpl;
-                xlean[t] &= tm > 0 && tm < 1000;
-                gp->mix = gp->mix || tm >= 1000;
+                xlean[t] &= allow && tm > 0;
+                mx = mx || tm >= 1000;
             }
+            gp->mix = gp->mix || mx;
+            (xlean[t] ? mix_lean : mix_full) |= mx;
             any_lean = any_lean || xlean[t];
             all_lean = all_lean && xlean[t];
         }
-        if (!gp->lean) {
-            any_lean = all_lean = false;
-        }
+        const bool split = any_lean && !all_lean && env_i("B300FFT_G_SPLIT", 1) != 0;
+        if (any_lean && !all_lean && !split) mix_full = gp->mix;  // everything in the full executor
         gp->lean = all_lean;
-        if (any_lean && !all_lean && env_i("B300FFT_G_SPLIT", 1) != 0) {
+        gp->kfull = mix_full ? GK_MIX : GK_BASE;
+        gp->klean = mix_lean ? GK_LEANMIX : GK_LEAN;
+        if (split) {
             std::vector<uint64_t> rest, lean;
             for (uint64_t it : items_lag) (xlean[it >> 32] ? lean : rest).push_back(it);
             gp->nrest = (int)rest.size();
@@ -861,8 +872,8 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
     if (cudaMalloc(&gp->ctl, sizeof(int) * (size_t)(2 + ctr)) != cudaSuccess) return FFT_ERR_ALLOC;
     gp->work_bytes = (size_t)woff * sizeof(float2);
     if (woff > 0 && cudaMalloc(&gp->work, gp->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
-    int bps[3] = {0, 0, 0}, dev = 0, sms = 0;
-    for (int k = 0; k < 3; ++k) {
+    int bps[4] = {0, 0, 0, 0}, dev = 0, sms = 0;
+    for (int k = 0; k < 4; ++k) {
         const void* kfn = gexec_fn(k);
         if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, gexec_smem(k)) != cudaSuccess)
             return FFT_ERR_CUDA;
@@ -877,7 +888,7 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
         gp->grid = gp->nitems;  // placeholders for gexec_parts
         const int np = gexec_parts(gp, parts);
         gp->grid = std::max(1, std::min(parts[0].nitems, sms * bps[parts[0].kind]));
-        gp->grid_lean = np > 1 ? std::max(1, std::min(parts[1].nitems, sms * bps[GK_LEAN])) : 0;
+        gp->grid_lean = np > 1 ? std::max(1, std::min(parts[1].nitems, sms * bps[gp->klean])) : 0;
     }
     gp->spin_limit = env_i("B300FFT_SPIN_LIMIT", 1 << 23);
     gp->use_graph = env_i("B300FFT_GRAPH", 1) != 0;
@@ -968,10 +979,11 @@ fft_status graph_plan_exec(GraphPlan* gp, const float2* in, float2* out, bool in
                            bool per_stage) {
     cudaError_t e = cudaSuccess;
     if (per_stage) {
-        const int k = gp->mix ? GK_MIX : (gp->lean ? GK_LEAN : GK_BASE);
+        // one kernel for every group: the lean one only when it covers every transform
+        const int k = gp->lean ? gp->klean : (gp->mix ? GK_MIX : GK_BASE);
         for (auto& g : gp->groups) {
             GExecArgs a = make_args(gp, in, out, inv, d_status, 1, g.first);
-            launch_gexec(k, g.second - g.first, a, st);  // a split plan is not lean: the full executor
+            launch_gexec(k, g.second - g.first, a, st);
             e = cudaGetLastError();
             if (e != cudaSuccess) return FFT_ERR_CUDA;
         }

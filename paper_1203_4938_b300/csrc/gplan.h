@@ -44,11 +44,16 @@ struct GraphPlan {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphNode_t knode[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [direction][launch]
     bool use_graph = true;
-    bool mix = false;   // has compile-time mixed-radix stages: runs the executor built with them
-    bool lean = false;  // templated power-of-two stages only: runs the lean executor (4 CTAs per SM)
-    // Plans where only some transforms qualify for the lean executor run two
-    // persistent launches: the first nrest queue items (the other transforms)
-    // in the full executor, then the rest in the lean one (grid_lean CTAs).
+    // Executor instantiations (generic.cuh): transforms whose stages are all
+    // compile-time tiles run in a lean executor without the runtime tiles
+    // (4 CTAs per SM), the others in the full one; either kind includes the
+    // mixed-radix tiles only when its transforms need them.  A plan with both
+    // kinds runs two persistent launches: the first nrest queue items in the
+    // full executor (kfull, grid CTAs), then the rest in the lean one (klean,
+    // grid_lean CTAs).
+    bool mix = false;   // some stage uses the compile-time mixed-radix tiles
+    bool lean = false;  // every transform runs in the lean executor
+    int kfull = 0, klean = 0;
     int nrest = 0, grid_lean = 0;
     int64_t spin_limit = int64_t(1) << 23;
     std::string desc;
