@@ -58,7 +58,8 @@ struct GStage {
     int sh;
     int tmpl;  // > 0: templated tiles: 2 * log2 N + (0: A, 1: B) of a power-of-two four-step,
                // 100 + log2 N2: second stage (rows of 2^L2) of a mixed-length four-step,
-               // 1000 + 16 M + K: single-tile lines of M * 2^K (compile-time mixed radix),
+               // 1000 + 16 M + K: single-tile lines of M * 2^K (compile-time passes; M = 1:
+               // a power of two),
                // 2000 + 16 M + A: four-step first stage, columns of M * 2^A (compile-time)
     int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
@@ -391,7 +392,7 @@ __device__ __noinline__ void g_mixed_cols(const float2* gin, float2* gout, int64
 // Compile-time mixed tiles of the stage graph (the lengths of the batched
 // mixed-radix kernels; columns M * 2^A with the same widths).
 #define B300_G_MIXED_ROWS(X)                                                                                    \
-    X(3, 0) X(3, 1) X(3, 2) X(3, 3) X(3, 4) X(3, 5) X(3, 6) X(3, 7) X(3, 8) X(3, 9) X(3, 10) X(5, 0) X(5, 1)    \
+    X(1, 4) X(1, 5) X(1, 6) X(1, 7) X(1, 8) X(1, 9) X(1, 10) X(1, 11) X(1, 12) X(3, 0) X(3, 1) X(3, 2) X(3, 3) X(3, 4) X(3, 5) X(3, 6) X(3, 7) X(3, 8) X(3, 9) X(3, 10) X(5, 0) X(5, 1)    \
     X(5, 2) X(5, 3) X(5, 4) X(5, 5) X(5, 6) X(5, 7) X(5, 8) X(5, 9) X(7, 0) X(7, 1) X(7, 2) X(7, 3) X(7, 4)     \
     X(7, 5) X(7, 6) X(7, 7) X(7, 8) X(7, 9)
 #define B300_G_MIXED_COLS(X)                                                                           \

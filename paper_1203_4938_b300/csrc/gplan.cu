@@ -191,7 +191,14 @@ struct Builder {
 // Compile-time mixed tiles (B300FFT_G_MIXT=0 turns them off): lines of
 // L = M * 2^K <= 4096, and four-step columns of M * 2^A with a column width.
 bool mixed_rows_templated(int64_t n, int* m, int* k) {
-    return env_i("B300FFT_G_MIXT", 1) != 0 && mixed_supported(n, m, k);
+    if (env_i("B300FFT_G_MIXT", 1) == 0) return false;
+    if (n >= 16 && n <= 4096 && (n & (n - 1)) == 0) {  // power-of-two lines: M = 1
+        *m = 1;
+        *k = 0;
+        while ((int64_t(1) << *k) < n) ++*k;
+        return true;
+    }
+    return mixed_supported(n, m, k);
 }
 bool mixed_cols_templated(int64_t n1, int64_t n2, int* m, int* a, int* width) {
     if (env_i("B300FFT_G_MIXT", 1) == 0 || !mixed_supported(n1, m, a)) return false;

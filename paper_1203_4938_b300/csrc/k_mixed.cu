@@ -115,12 +115,41 @@ cudaError_t one(int op, bool inv, const float2* in, float2* out, int64_t nrows, 
     return cudaGetLastError();
 }
 
+// Tables of the power-of-two lines the stage-graph executor runs with the
+// same compile-time passes (M = 1): no kernel of their own.
+template <int K>
+cudaError_t pow2_lines_table(int op, float2* out, cudaStream_t st, int* info) {
+    using MP = MixPlan<1, K>;
+    if (op == 0) {
+        info[0] = MP::TWSIZE;
+        info[1] = MP::NL;
+        return cudaSuccess;
+    }
+    if (op != 1) return cudaErrorInvalidValue;
+    for (int p = 1; p < MP::NPASS; ++p) {
+        cudaError_t e = gen_pass_table(out + MP::twoff(p), MP::ns(p), MP::radix(p), st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t dispatch(int m, int k, int op, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
                      cudaStream_t st, int* info) {
 #define B300_X(M, K) \
     if (m == M && k == K) return one<M, K>(op, inv, in, out, nrows, tw, st, info);
     B300_MIXED_CASES(B300_X)
 #undef B300_X
+    if (m == 1) {
+        switch (k) {
+#define B300_P(K) \
+    case K:       \
+        return pow2_lines_table<K>(op, out, st, info);
+            B300_P(4) B300_P(5) B300_P(6) B300_P(7) B300_P(8) B300_P(9) B300_P(10) B300_P(11) B300_P(12)
+#undef B300_P
+            default:
+                break;
+        }
+    }
     return cudaErrorInvalidValue;
 }
 }  // namespace

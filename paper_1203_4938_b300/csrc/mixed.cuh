@@ -1,5 +1,6 @@
 // mixed.cuh -- batched transforms of mixed-radix lengths L = M * 2^K <= 4096
-// (M = 3, 5, 7) with every radix, stride and index known at compile time:
+// (M = 3, 5, 7; M = 1, a power of two, serves the stage-graph executor's
+// single-tile lines) with every radix, stride and index known at compile time:
 // the Cooley-Tukey split of Sec. III-A applied to the factors 16, ..., 16,
 // 2^(K mod 4), M in turn, in self-sorting Stockham order.
 //
@@ -34,11 +35,11 @@ namespace b300fft {
 
 template <int M, int K, int NL_ = 4096 / (M << K)>
 struct MixPlan {
-    static_assert(M == 3 || M == 5 || M == 7, "odd factor 3, 5 or 7");
+    static_assert(M == 3 || M == 5 || M == 7 || (M == 1 && K >= 1), "odd factor 3, 5 or 7 (1: a power of two)");
     static constexpr int L = M << K;
     static_assert(L <= 4096, "one tile per line");
     static constexpr int NP16 = K / 4, REM = K % 4;
-    static constexpr int NPASS = NP16 + (REM ? 1 : 0) + 1;
+    static constexpr int NPASS = NP16 + (REM ? 1 : 0) + (M > 1 ? 1 : 0);
     __host__ __device__ static constexpr int radix(int p) {
         return p < NP16 ? 16 : ((REM && p == NP16) ? (1 << REM) : M);
     }
