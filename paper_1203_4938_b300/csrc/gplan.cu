@@ -946,22 +946,45 @@ cudaError_t ensure_graph(GraphPlan* gp, bool inv, const GExecArgs& a) {
     if (gp->gexec[d]) return cudaSuccess;
     GPart parts[2];
     const int np = gexec_parts(gp, parts);
-    cudaStream_t cs;
+    // two launches sit on parallel branches of the graph (their transforms do
+    // not depend on each other): the lean one takes the SMs the full one
+    // leaves idle while its last dependency chains finish
+    const bool par = np == 2 && env_i("B300FFT_G_PARALLEL", 1) != 0;
+    cudaStream_t cs, cs2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (par) {
+        if (cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming) != cudaSuccess)
+            e = cudaErrorMemoryAllocation;
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaMemsetAsync(gp->ctl, 0, sizeof(int) * (size_t)(2 + gp->ncounters), cs);
+        if (par) {
+            cudaEventRecord(ev0, cs);
+            cudaStreamWaitEvent(cs2, ev0, 0);
+        }
         for (int i = 0; i < np; ++i) {
             GExecArgs b = a;
             b.items += parts[i].item0;
             b.nitems = parts[i].nitems;
             b.qhead = gp->ctl + parts[i].head;
-            launch_gexec(parts[i].kind, parts[i].grid, b, cs);
+            launch_gexec(parts[i].kind, parts[i].grid, b, par && i == 1 ? cs2 : cs);
         }
-        e = cudaStreamEndCapture(cs, &gp->graph[d]);
+        if (par) {
+            cudaEventRecord(ev1, cs2);
+            cudaStreamWaitEvent(cs, ev1, 0);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &gp->graph[d]);
+        e = cudaGetLastError() != cudaSuccess ? cudaErrorUnknown : e2;
     }
     cudaStreamDestroy(cs);
+    if (cs2) cudaStreamDestroy(cs2);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     if (e != cudaSuccess) return e;
     size_t nn = 0;
     cudaGraphGetNodes(gp->graph[d], nullptr, &nn);
