@@ -46,7 +46,8 @@ struct fft_plan_s {
     // power-of-two kernels
     int logn_a = 0, logn_b = 0, sh = 0;
     int mix_m = 0;  // RowsMixed: L = mix_m * 2^logn_a
-    int mix_mh = 0, mix_mw = 0;  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
+    int mix_mh = 0, mix_mw = 0;
+    bool real_fused = false;  // Real: one-pass fused rows + split kernel (h = 2^5 .. 2^12)  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
     int cols_c = 0;     // columns kernel width
     int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA
 

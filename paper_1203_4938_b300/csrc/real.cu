@@ -13,12 +13,112 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 
 #include "butterfly.cuh"
 #include "launch.h"
 #include "plan.h"
+#include "stockham_pow2.cuh"
 
 namespace b300fft {
+
+// Fused forms for h = N/2 = 2^LOGN <= 4096 (one tile per transform, TPC
+// transforms per 256-thread CTA): the split happens inside the tile after
+// the last radix pass (Z[h-k] comes from the exchange buffer), the merge
+// inside the tile before the first one -- one HBM round trip instead of two.
+template <int LOGN, int TPC, bool C2R>
+__global__ void __launch_bounds__(RowsCfg<LOGN, TPC>::THREADS) k_real_rows(const float2* __restrict__ in,
+                                                                           float2* __restrict__ out, int64_t nrows,
+                                                                           const float2* __restrict__ tw,
+                                                                           const float2* __restrict__ w) {
+    using PL = P2Plan<LOGN>;
+    constexpr int h = PL::N, T = PL::T;
+    static_assert(PL::NPASS >= 2, "the exchange buffer carries the mirrored bins");
+    extern __shared__ float2 smem[];
+    const int t = threadIdx.x & (T - 1), sub = threadIdx.x / T;
+    const int64_t row = (int64_t)blockIdx.x * TPC + sub;
+    const bool ok = row < nrows;
+    float2* s = smem + sub * PL::PADDED;
+    float2 v[PL::R];
+    if constexpr (!C2R) {
+        const float2* src = in + row * h;
+#pragma unroll
+        for (int i = 0; i < PL::R; ++i) v[i] = ok ? __ldcs(src + t + i * T) : make_float2(0.f, 0.f);
+        run_passes<PL, 0, false, false, 1>(v, t, s, 0, tw);  // Z[t + i T]; the exchange area is free again
+#pragma unroll
+        for (int i = 0; i < PL::R; ++i) s[padi(t + i * T)] = v[i];
+        __syncthreads();
+        if (ok) {
+            float2* dst = out + row * (h + 1);
+#pragma unroll
+            for (int i = 0; i < PL::R; ++i) {
+                const int k = t + i * T;
+                const float2 zk = v[i], zm = s[padi((h - k) & (h - 1))];
+                const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+                __stcs(dst + k, cadd(e, cmul(o, __ldg(w + k))));
+            }
+            if (t == 0) __stcs(dst + h, make_float2(v[0].x - v[0].y, 0.f));  // X[h] = E[0] - O[0]
+        }
+    } else {
+        const float2* src = in + row * (h + 1);
+#pragma unroll
+        for (int i = 0; i < PL::R; ++i) {
+            const int k = t + i * T;
+            float2 z = make_float2(0.f, 0.f);
+            if (ok) {
+                const float2 xk = __ldg(src + k), xm = __ldg(src + h - k);
+                const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);                       // X[k] + conj(X[h-k])
+                const float2 o = cmulc(make_float2(xk.x - xm.x, xk.y + xm.y), __ldg(w + k));  // (X[k] - conj) W^-k
+                z = make_float2(e.x - o.y, e.y + o.x);                                        // E + i O
+            }
+            v[i] = z;
+        }
+        run_passes<PL, 0, true, false, 1>(v, t, s, 0, tw);
+        if (ok) {
+            float2* dst = out + row * h;
+#pragma unroll
+            for (int i = 0; i < PL::R; ++i) __stcs(dst + t + i * T, v[i]);
+        }
+    }
+}
+
+namespace {
+template <int LOGN>
+cudaError_t real_rows_one(bool prep, bool c2r, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                          const float2* w, cudaStream_t st) {
+    constexpr int TPC = (256 >> (LOGN - 4)) > 0 ? (256 >> (LOGN - 4)) : 1;  // 256 threads per CTA
+    using CF = RowsCfg<LOGN, TPC>;
+    if (prep) {
+        cudaError_t e = cudaFuncSetAttribute(k_real_rows<LOGN, TPC, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_real_rows<LOGN, TPC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     CF::SMEM);
+        return e;
+    }
+    if (nrows <= 0) return cudaSuccess;
+    const int64_t g = (nrows + TPC - 1) / TPC;
+    if (g > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (c2r) k_real_rows<LOGN, TPC, true><<<(unsigned)g, CF::THREADS, CF::SMEM, st>>>(in, out, nrows, tw, w);
+    else k_real_rows<LOGN, TPC, false><<<(unsigned)g, CF::THREADS, CF::SMEM, st>>>(in, out, nrows, tw, w);
+    return cudaGetLastError();
+}
+
+// log2 h with a fused kernel (one tile per transform, at least two passes)
+cudaError_t real_rows(int logh, bool prep, bool c2r, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                      const float2* w, cudaStream_t st) {
+    switch (logh) {
+#define B300_C(L) \
+    case L:       \
+        return real_rows_one<L>(prep, c2r, in, out, nrows, tw, w, st);
+        B300_C(5) B300_C(6) B300_C(7) B300_C(8) B300_C(9) B300_C(10) B300_C(11) B300_C(12)
+#undef B300_C
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
 
 // Z (batch x h, complex, natural order) -> X (batch x (h+1)); h = N/2.
 __global__ void k_r2c_split(const float2* __restrict__ z, float2* __restrict__ x, int64_t h, int64_t batch,
@@ -87,6 +187,17 @@ fft_status build_real_plan(fft_plan_s* p, int64_t n, int64_t batch) {
     p->kernels = 1 + fft_plan_kernel_count(p->inner);
     char inner[200];
     fft_plan_describe(p->inner, inner, sizeof inner);
+    // h = 2^5 .. 2^12 with the single-pass complex plan: the fused kernels
+    const char* fz = std::getenv("B300FFT_REAL_FUSED");
+    p->real_fused = (!fz || std::atoi(fz) != 0) && p->inner->kind == PlanKind::Rows && p->inner->logn_a >= 5 &&
+                    p->inner->logn_a <= 12 &&
+                    real_rows(p->inner->logn_a, true, false, nullptr, nullptr, 0, nullptr, nullptr, 0) == cudaSuccess;
+    if (p->real_fused) {
+        p->kernels = 1;
+        std::snprintf(p->desc, sizeof p->desc, "real N=%lld fused (complex N/2 = 2^%d rows + split in one pass)",
+                      (long long)n, p->inner->logn_a);
+        return FFT_OK;
+    }
     std::snprintf(p->desc, sizeof p->desc, "real N=%lld via complex N/2 [%s] + split", (long long)n, inner);
     return FFT_OK;
 }
@@ -97,6 +208,13 @@ fft_status exec_real(fft_plan_s* p, const void* in, void* out, bool inv, cudaStr
     const int64_t h = p->len[0] / 2, batch = p->batch;
     float2* z = p->d_work;
     unsigned g;
+    if (p->real_fused && in != out) {  // in place: the two-pass form (a fused tile would overwrite unread rows)
+        const fft_plan_s* q = p->inner;
+        return real_rows(q->logn_a, false, inv, static_cast<const float2*>(in), static_cast<float2*>(out), batch,
+                         q->d_tables + q->off_a, p->d_tables, st) == cudaSuccess
+                   ? FFT_OK
+                   : FFT_ERR_CUDA;
+    }
     if (!inv) {
         // real x viewed as h complex values per transform (x[2n] + i x[2n+1])
         fft_status s = fft_exec(p->inner, in, z, FFT_FORWARD, st);

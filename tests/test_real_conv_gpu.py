@@ -32,6 +32,55 @@ def test_r2c_c2r(torch, n, batch):
     assert max_rel_l2((y.cpu().numpy() / n).astype(np.complex128), xr.astype(np.complex128), -1) <= 2 * TOL_FP32
 
 
+@pytest.mark.parametrize("logh", [5, 6, 7, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("fused", ["1", "0"])
+def test_r2c_c2r_fused_range(torch, monkeypatch, logh, fused):
+    """n = 2h with h = 2^5..2^12: one fused pass per direction (split /
+    merge inside the tile), or the two-pass form when switched off; the batch
+    leaves the last CTA partly empty."""
+    from paper_1203_4938_b300 import fft as F
+    monkeypatch.setenv("B300FFT_REAL_FUSED", fused)
+    h = 1 << logh
+    n = 2 * h
+    tpc = max(1, 256 // (h // 16))
+    batch = 2 * tpc + 1
+    rng = np.random.default_rng(logh)
+    xr = rng.standard_normal((batch, n)).astype(np.float32)
+    ref = oracle.fft(xr.astype(np.complex128), -1)[:, : n // 2 + 1]
+    with F.RealPlan(n, batch) as p:
+        assert ("fused" in p.describe()) == (fused == "1"), p.describe()
+        X = p.forward(torch.from_numpy(xr).cuda())
+        torch.cuda.synchronize()
+        assert max_rel_l2(X.cpu().numpy(), ref, -1) <= TOL_FP32
+        y = p.inverse(X)
+        torch.cuda.synchronize()
+        p.check()
+    assert max_rel_l2((y.cpu().numpy() / n).astype(np.complex128), xr.astype(np.complex128), -1) <= 2 * TOL_FP32
+
+
+@pytest.mark.parametrize("n", [256, 4096])
+def test_r2c_c2r_in_place(torch, n):
+    """in == out (the buffer holds batch * (n/2+1) complex values): the fused
+    plan falls back to the two-pass form, which reads its input first."""
+    from paper_1203_4938_b300 import fft as F
+    batch, h = 5, n // 2
+    rng = np.random.default_rng(n)
+    xr = rng.standard_normal((batch, n)).astype(np.float32)
+    ref = oracle.fft(xr.astype(np.complex128), -1)[:, : h + 1]
+    buf = torch.zeros(batch * (h + 1), dtype=torch.complex64, device="cuda")
+    buf.view(torch.float32)[: batch * n].copy_(torch.from_numpy(xr.reshape(-1)).cuda())
+    with F.RealPlan(n, batch) as p:
+        assert "fused" in p.describe()
+        assert F.fft_exec(p.handle, buf.data_ptr(), buf.data_ptr(), F.FFT_FORWARD) == F.FFT_OK
+        torch.cuda.synchronize()
+        assert max_rel_l2(buf.view(batch, h + 1).cpu().numpy(), ref, -1) <= TOL_FP32
+        assert F.fft_exec(p.handle, buf.data_ptr(), buf.data_ptr(), F.FFT_INVERSE) == F.FFT_OK
+        torch.cuda.synchronize()
+        p.check()
+    y = buf.view(torch.float32)[: batch * n].cpu().numpy().reshape(batch, n) / n
+    assert max_rel_l2(y.astype(np.complex128), xr.astype(np.complex128), -1) <= 2 * TOL_FP32
+
+
 def test_c2r_of_oracle_half_spectrum(torch):
     """C2R alone, fed the oracle's half spectrum of a real signal."""
     from paper_1203_4938_b300 import fft as F
