@@ -117,6 +117,22 @@ FFT_API fft_plan fft_plan_create_real(int64_t n, int64_t batch);
 FFT_API fft_status fft_spectrum_product(const void *a, const void *b, void *out, int64_t n, int64_t batch,
                                         float scale, int conj_b, void *stream);
 
+/* FFT convolution / correlation of every row in one call (Sec. III-A names
+ * convolution among the DFT's uses):
+ *     out[t] = scale * IDFT( DFT(x[t]) * H )          (conj_h = 0)
+ *     out[t] = scale * IDFT( DFT(x[t]) * conj(H) )    (conj_h != 0)
+ * with the unnormalised transforms of `plan` (a 1-D FP32 complex plan of n
+ * points and batch rows; ragged and real plans: FFT_ERR_INVALID_ARG).
+ * x, out: [batch][n] complex64; hspec: H = DFT(h), [n] complex64; device
+ * pointers, 16-byte aligned; out == x allowed.  scale = 1/n gives the
+ * circular convolution (correlation) of x with h.  Plans of a power of two
+ * n <= 2^14 run one fused pass per row (forward passes, product, inverse
+ * passes in the tile: one HBM round trip); other plans run the forward
+ * transform, fft_spectrum_product and the inverse transform through `out`.
+ * Asynchronous on `stream`; allocates nothing. */
+FFT_API fft_status fft_convolve(fft_plan plan, const void *x, const void *hspec, void *out, float scale, int conj_h,
+                                void *stream);
+
 /* The GPU steps of the image example (Sec. III-B), fused in one pass (no
  * paper formulas are given; the readings below are the standard ones):
  *   1. JFIF (ITU-R BT.601 full range) YCbCr of 8-bit RGB:

@@ -754,6 +754,31 @@ fft_status fft_exec(fft_plan plan, const void* in, void* out, int direction, voi
                      static_cast<cudaStream_t>(stream));
 }
 
+fft_status fft_convolve(fft_plan plan, const void* x, const void* hspec, void* out, float scale, int conj_h,
+                        void* stream) {
+    if (!is_registered(plan)) return FFT_ERR_BAD_HANDLE;
+    if (!x || !hspec || !out) return FFT_ERR_INVALID_ARG;
+    if (plan->dims != 1 || plan->precision != FFT_FP32 || plan->kind == PlanKind::Ragged ||
+        plan->kind == PlanKind::Real)
+        return FFT_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(hspec) & 15) ||
+        (reinterpret_cast<uintptr_t>(out) & 15))
+        return FFT_ERR_MISALIGNED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float2* in = static_cast<const float2*>(x);
+    float2* o = static_cast<float2*>(out);
+    const float2* hs = static_cast<const float2*>(hspec);
+    if (plan->kind == PlanKind::Rows)  // one fused pass
+        return launch_conv_rows(plan->logn_a, conj_h != 0, in, o, plan->batch, plan->d_tables + plan->off_a, hs,
+                                scale, st) == cudaSuccess
+                   ? FFT_OK
+                   : FFT_ERR_CUDA;
+    fft_status s = exec_plan(plan, in, o, false, st);
+    if (s == FFT_OK) s = fft_spectrum_product(o, hs, o, plan->len[0], plan->batch, scale, conj_h, stream);
+    if (s == FFT_OK) s = exec_plan(plan, o, o, true, st);
+    return s;
+}
+
 fft_status fft_exec_kernel(fft_plan plan, int k, const void* in, void* out, int direction, void* stream) {
     if (!is_registered(plan)) return FFT_ERR_BAD_HANDLE;
     if (k < 0 || k >= plan->kernels) return FFT_ERR_INVALID_ARG;

@@ -50,6 +50,11 @@ cudaError_t launch_cols2d_mixed(int m, int k, bool inv, const float2* in, float2
 cudaError_t launch_cols_mixed(int m, int a, bool inv, const float2* in, float2* out, int64_t S2, int64_t items,
                               const float2* tw, const float2* lo, const float2* hi, int sh, cudaStream_t st);
 
+// One-pass FFT convolution of rows of 2^logn (conv.cu): forward passes, times
+// hs (or conj(hs)) and scale, inverse passes; tw = the rows plan's table.
+cudaError_t launch_conv_rows(int logn, bool corr, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                             const float2* hs, float scale, cudaStream_t st);
+
 cudaError_t launch_rows(int logn, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
                         cudaStream_t st);
 

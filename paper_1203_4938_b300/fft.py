@@ -43,7 +43,7 @@ EXPORTS = ("fft_plan_create", "fft_plan_create_ragged", "fft_last_error", "fft_e
            "fft_plan_check", "fft_plan_destroy", "fft_plan_workspace_bytes", "fft_status_string",
            "fft_plan_kernel_count", "fft_plan_describe", "fft_exec_kernel", "fft_exec_per_size",
            "fft_exec_pow2_static", "fft_plan_create_real", "fft_spectrum_product", "fft_image_steps",
-           "fft_probe_fma")
+           "fft_probe_fma", "fft_convolve")
 
 _lock = threading.Lock()
 _lib = None
@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fft_image_steps.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
                                         ctypes.c_float, vp, vp, vp, vp, vp]
         lib.fft_image_steps.restype = ctypes.c_int
+        lib.fft_convolve.argtypes = [vp, vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]
+        lib.fft_convolve.restype = ctypes.c_int
         lib.fft_probe_fma.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp]
         lib.fft_probe_fma.restype = ctypes.c_int
         lib.fft_plan_create_real.argtypes = [ctypes.c_int64, ctypes.c_int64]
@@ -141,6 +143,10 @@ def fft_image_steps(rgb_ptr: int, batch: int, h: int, w: int, ux: float, uy: flo
                     cr_ptr: int, d_ptr: int, stream: int = 0) -> int:
     return int(load().fft_image_steps(rgb_ptr, int(batch), int(h), int(w), float(ux), float(uy), y_ptr, cb_ptr,
                                       cr_ptr, d_ptr, stream or None))
+
+
+def fft_convolve(plan, x_ptr: int, h_ptr: int, out_ptr: int, scale: float, conj_h: bool, stream: int = 0) -> int:
+    return int(load().fft_convolve(plan, x_ptr, h_ptr, out_ptr, float(scale), int(bool(conj_h)), stream or None))
 
 
 def fft_probe_fma(out_ptr: int, blocks: int, iters: int, stream: int = 0) -> int:
@@ -389,9 +395,15 @@ def convolve(x, h, corr: bool = False):
     for v in shape:
         n *= v
     with Plan(shape, batch) as px, Plan(shape, 1) as ph:
-        X = px.forward(x)
         H = ph.forward(h.reshape((1,) + shape).contiguous())
         s = torch.cuda.current_stream(x.device)
+        if len(shape) == 1:  # one call: fused for power-of-two lengths up to 2^14
+            out = torch.empty_like(x)
+            rc = fft_convolve(px.handle, x.data_ptr(), H.data_ptr(), out.data_ptr(), 1.0 / n, corr, s.cuda_stream)
+            if rc != FFT_OK:
+                raise FFTError(rc, "fft_convolve")
+            return out
+        X = px.forward(x)
         rc = fft_spectrum_product(X.data_ptr(), H.data_ptr(), X.data_ptr(), n, batch, 1.0 / n, corr, s.cuda_stream)
         if rc != FFT_OK:
             raise FFTError(rc, "fft_spectrum_product")

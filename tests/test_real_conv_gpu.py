@@ -127,3 +127,41 @@ def test_convolution_2d_image_blur(torch):
         for dx in (-1, 0, 1):
             ref += np.roll(img.astype(np.complex128), (dy, dx), axis=(1, 2)) / 9
     assert max_rel_l2(y.reshape(2, -1), ref.reshape(2, -1), -1) <= 2 * TOL_FP32
+
+
+@pytest.mark.parametrize("n,batch", [(8, 3), (1024, 5), (4096, 7), (8192, 3), (16384, 2), (1000, 3), (1 << 16, 2),
+                                     (3 * 1024, 4)])
+@pytest.mark.parametrize("corr", [False, True])
+def test_fft_convolve_one_call(torch, n, batch, corr):
+    """fft_convolve against the oracle's circular convolution / correlation:
+    one fused pass for powers of two <= 2^14, the three-step form otherwise;
+    out == x in place on the second call."""
+    from paper_1203_4938_b300 import fft as F
+    rng = np.random.default_rng(n * 3 + batch)
+    x = (rng.standard_normal((batch, n)) + 1j * rng.standard_normal((batch, n))).astype(np.complex64)
+    h = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    ref = oracle.circ_conv(x, h, corr) if n <= 8192 else None
+    with F.Plan((n,), batch) as p, F.Plan((n,), 1) as ph:
+        H = ph.forward(to_dev(h.reshape(1, n)))
+        xd = to_dev(x)
+        out = torch.empty_like(xd)
+        s = torch.cuda.current_stream().cuda_stream
+        assert F.fft_convolve(p.handle, xd.data_ptr(), H.data_ptr(), out.data_ptr(), 1.0 / n, corr, s) == F.FFT_OK
+        assert F.fft_convolve(p.handle, xd.data_ptr(), H.data_ptr(), xd.data_ptr(), 1.0 / n, corr, s) == F.FFT_OK
+        torch.cuda.synchronize()
+        y, y2 = out.cpu().numpy(), xd.cpu().numpy()
+    if ref is None:  # long rows: the convolution theorem against the oracle's transforms
+        X = oracle.fft(x, -1)
+        Hh = oracle.fft(h[None], -1)[0]
+        ref = oracle.fft(X * (np.conj(Hh) if corr else Hh), +1) / n
+    assert max_rel_l2(y, ref, -1) <= 4 * TOL_FP32, (n, corr)
+    assert np.array_equal(y, y2)
+
+
+def test_fft_convolve_rejects_ragged_and_real(torch):
+    from paper_1203_4938_b300 import fft as F
+    buf = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+    with F.Ragged([64, 128]) as r, F.RealPlan(64, 1) as q:
+        for p in (r, q):
+            assert F.fft_convolve(p.handle, buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), 1.0, False) == \
+                F.FFT_ERR_INVALID_ARG
