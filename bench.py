@@ -39,12 +39,29 @@ METRIC = "C2C FFT GFLOP/s (5N*log2N/t), fwd+inv sweep N=2^10..2^24, 2^26 complex
 # of each sweep size's kernel at the full sweep size (2^26 elements), from the
 # single-pass ncu launch list of `python bench.py --steps 1 --warmup 1 --no-e2e
 # --no-cpu` (mean of the forward and inverse launches).  The numbers belong to
-# the kernel sources hashed in TRAFFIC_SOURCES; when those files change the
+# the kernel sources hashed in TRAFFIC_SOURCES and to the plans described in
+# MEASURED_PLANS (split, tile shape, chunking); when either differs the
 # benchmark reports the traffic as null until a new capture replaces them.
 MEASURED_DRAM_MB = {10: 1018, 11: 1020, 12: 1020, 13: 1022, 14: 1021, 15: 1356, 16: 1017, 17: 1420, 18: 1457, 19: 1023, 20: 1125, 21: 1396, 22: 1356, 23: 2017, 24: 2167}
+MEASURED_PLANS = {
+    10: "rows N=2^10 tpc=4 threads=256",
+    11: "rows N=2^11 tpc=2 threads=256",
+    12: "rows N=2^12 tpc=1 threads=256",
+    13: "rows N=2^13 tpc=1 threads=256",
+    14: "rows N=2^14 tpc=1 threads=512",
+    15: "fourstep-persist N=2^15 = 2^7 (C=32) x 2^8 (tpc=16) threads=256 grid=592 chunk=128 x 16",
+    16: "fourstep-persist N=2^16 = 2^8 (C=16) x 2^8 (tpc=16) threads=256 grid=592 chunk=32 x 32",
+    17: "fourstep-persist N=2^17 = 2^8 (C=16) x 2^9 (tpc=8) threads=256 grid=592 chunk=32 x 16",
+    18: "fourstep-persist N=2^18 = 2^8 (C=16) x 2^10 (tpc=4) threads=256 grid=592 chunk=16 x 16",
+    19: "fourstep-persist N=2^19 = 2^9 (C=16) x 2^10 (tpc=8) threads=512 grid=296 chunk=4 x 32",
+    20: "fourstep-persist N=2^20 = 2^10 (C=8) x 2^10 (tpc=8) threads=512 grid=296 chunk=2 x 32",
+    21: "threestep N=2^21 = 2^7 x (2^7 x 2^7) threads=256 grid=592 chunk=2 x 16 groups=8 ahead=8",
+    22: "threestep N=2^22 = 2^7 x (2^7 x 2^8) threads=256 grid=592 chunk=1 x 16 groups=8 ahead=8",
+    23: "threestep N=2^23 = 2^8 x (2^7 x 2^8) threads=256 grid=592 chunk=1 x 8 groups=16 ahead=10",
+    24: "threestep N=2^24 = 2^8 x (2^8 x 2^8) threads=256 grid=592 chunk=1 x 4 groups=16 ahead=5"}
 TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threestep.cuh", "kernels_launch.cuh",
-                   "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu", "fft_api.cu", "exec.cu"]
-TRAFFIC_SOURCES_SHA = "279f07e7311b32b2"
+                   "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu"]
+TRAFFIC_SOURCES_SHA = "5320d4467e90d0f2"
 
 
 def traffic_sources_sha() -> str:
@@ -57,13 +74,16 @@ def traffic_sources_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(logn: int):
+def measured_traffic(logn: int, plan_desc: str):
     """DRAM bytes per launch of the sweep kernel for 2^logn, or None when the
-    kernel sources differ from the captured ones (or the size was not captured)."""
+    kernel sources or the plan differ from the captured ones (or the size was
+    not captured)."""
     try:
         if traffic_sources_sha() != TRAFFIC_SOURCES_SHA:
             return None
     except OSError:
+        return None
+    if MEASURED_PLANS.get(logn) != plan_desc:
         return None
     mb = MEASURED_DRAM_MB.get(logn)
     return None if mb is None else mb * 1e6
@@ -397,7 +417,7 @@ def run_gpu(args):
 
     if rank == 0:
         kname = plans[di].describe()
-        traffic = measured_traffic(int(math.log2(dn))) if db << int(math.log2(dn)) == 1 << TOTAL_LOG2 else None
+        traffic = measured_traffic(int(math.log2(dn)), kname) if db << int(math.log2(dn)) == 1 << TOTAL_LOG2 else None
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -417,6 +437,7 @@ def run_gpu(args):
                             "sweep_nominal_tflops": value / 1e3, "nominal_frac": value / 1e3 / fma_tflops,
                             "note": "nominal 5N log2 N flops per transform against the measured FP32 FMA "
                                     "rate (probe kernel); the sweep is bounded by HBM, not by this"},
+            "per_size_plan": {f"2^{sizes[i][0]}": plans[i].describe() for i in range(len(sizes))},
             "per_size_ms": {f"2^{sizes[i][0]}": sum(statistics.mean(per[(i, kk)]) for kk in
                                                    range(plans[i].kernel_count)) * 2 for i in range(len(sizes))},
         }
