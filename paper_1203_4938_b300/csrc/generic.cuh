@@ -60,7 +60,8 @@ struct GStage {
                // 100 + log2 N2: second stage (rows of 2^L2) of a mixed-length four-step,
                // 1000 + 16 M + K: single-tile lines of M * 2^K (compile-time passes; M = 1:
                // a power of two),
-               // 2000 + 16 M + A: four-step first stage, columns of M * 2^A (compile-time)
+               // 2000 + 16 M + A: four-step first stage, columns of M * 2^A (compile-time),
+               // 3000 + K2: four-step second stage, rows of 2^K2 with the transposed store
     int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
     int64_t pre_tab, post_tab;             // table offsets in the pool
@@ -345,7 +346,7 @@ static_assert(kGMixOffF2 * 8 + kGMaxLines * 8 <= kGSmem, "line offsets fit the e
 
 template <int L>
 struct MixRowsAt {  // line l, element e at base + off[l] + e
-    static constexpr bool LINE_FAST = false;
+    static constexpr bool LOAD_LF = false, STORE_LF = false;
     const float2* in;
     float2* out;
     const int64_t* off;
@@ -389,6 +390,32 @@ __device__ __noinline__ void g_mixed_cols(const float2* gin, float2* gout, int64
     }
 }
 
+// Rows of a four-step's second stage with the transposed store: line l
+// (row k1 = line0 + l of the [N1][L] work buffer) is read contiguously (b
+// fastest) and its bin e goes to out[k1 + N1 e] (line fastest: runs of up to
+// NL consecutive k1).
+template <int L>
+struct MixRowsT {
+    static constexpr bool LOAD_LF = false, STORE_LF = true;
+    const float2* in;  // work buffer at row line0
+    float2* out;       // output at k1 = line0
+    int64_t n1;
+    __device__ __forceinline__ float2 load(int line, int e) const { return __ldcg(in + line * L + e); }
+    __device__ __forceinline__ void store(int line, int e, float2 v) const { __stcs(out + line + n1 * e, v); }
+};
+
+template <int K2>
+__device__ __noinline__ void g_mixed_rowsT(const float2* gin, float2* gout, int64_t n1, int tile, int inv,
+                                           const float2* __restrict__ tw, float2* smem) {
+    using MP = MixPlan<1, K2, kGMixLines(1 << K2)>;
+    static_assert(MP::SMEM <= kGMixOffF2 * 8, "tile buffer below the line-offset table");
+    const int64_t line0 = (int64_t)tile * MP::NL;
+    const int nl = (int)(n1 - line0 < MP::NL ? n1 - line0 : MP::NL);
+    const MixRowsT<MP::L> io{gin + line0 * MP::L, gout + line0, n1};
+    if (inv) mix_pass<MP, 0, true>(io, smem, nl, tw);
+    else mix_pass<MP, 0, false>(io, smem, nl, tw);
+}
+
 // Compile-time mixed tiles of the stage graph (the lengths of the batched
 // mixed-radix kernels; columns M * 2^A with the same widths).
 #define B300_G_MIXED_ROWS(X)                                                                                    \
@@ -411,6 +438,12 @@ __device__ __forceinline__ void g_mixed_tile(const GExecArgs& a, const GTransfor
         break;
         B300_G_MIXED_ROWS(B300_R)
 #undef B300_R
+#define B300_T(K2)                                                                        \
+    case 3000 + K2:                                                                       \
+        g_mixed_rowsT<K2>(gin, gout, (int64_t)st.nlines, tile, st.inv, tw, smem);         \
+        break;
+        B300_T(5) B300_T(6) B300_T(7) B300_T(8) B300_T(9) B300_T(10) B300_T(11) B300_T(12)
+#undef B300_T
 #define B300_C(M, A, NL)                                                                                          \
     case 2000 + 16 * M + A:                                                                                       \
         g_mixed_cols<M, A, NL>(gin, gout, st.in_es, tile, st.inv, tw, a.pool + st.lo, a.pool + st.hi, st.sh, smem); \

@@ -353,10 +353,18 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
             // rows of 128 or 256 points and a line count the rows-per-tile divide:
             // the templated transposed-row tile (32 or 16 rows, 256 threads)
             const int tpc2 = n2 == 128 ? 32 : (n2 == 256 ? 16 : 0);
+            int l2 = 0;
+            while ((int64_t(1) << l2) < n2) ++l2;
             if (tpc2 && n1 % tpc2 == 0 && env_i("B300FFT_G_POW2T", 1) != 0) {
                 b.tmpl = 100 + (n2 == 128 ? 7 : 8);
                 b.ntiles = (int)(n1 / tpc2);
                 b.post_tab = B.pow2_table(n2 == 128 ? 7 : 8);
+            } else if ((int64_t(1) << l2) == n2 && l2 >= 5 && l2 <= 12 && env_i("B300FFT_G_MIXT", 1) != 0) {
+                // other power-of-two rows: the compile-time transposed-row tile
+                // (any line count; the last tile may hold fewer lines)
+                b.tmpl = 3000 + l2;
+                b.ntiles = (int)((n1 + kGMixLines((int)n2) - 1) / kGMixLines((int)n2));
+                b.pre_tab = B.mixed_table(1, l2);
             }
             (d ? i : f).push_back(a);
             (d ? i : f).push_back(b);

@@ -15,7 +15,9 @@
 //   MixCols  lines are adjacent columns of a row-major [L][S2] array (line
 //            fastest across threads), stored with the four-step twiddle
 //            W_N^{(col0 + line) e} -- the first pass of a four-step.
-// Middle passes map b fastest (shared memory only).
+// (the stage-graph executor adds rows with per-line offsets and rows with
+// the four-step's transposed store).  Middle passes map b fastest (shared
+// memory only).
 //
 // Butterfly b of pass p (k = b mod Ns) reads element b + r S of its line,
 // multiplies input r by W_{Ns R}^{k r} and writes output r to
@@ -101,7 +103,7 @@ __device__ __forceinline__ void mix_twiddle(float2* v, const float2* __restrict_
 // Contiguous rows: line l, element e at base + l L + e.
 template <int L>
 struct MixRows {
-    static constexpr bool LINE_FAST = false;
+    static constexpr bool LOAD_LF = false, STORE_LF = false;
     const float2* in;
     float2* out;
     __device__ __forceinline__ float2 load(int line, int e) const { return __ldcs(in + line * L + e); }
@@ -114,7 +116,7 @@ struct MixRows {
 // into the workspace); otherwise plain final stores (2-D column pass).
 template <bool INV, bool TW = true>
 struct MixCols {
-    static constexpr bool LINE_FAST = true;
+    static constexpr bool LOAD_LF = true, STORE_LF = true;
     const float2* in;
     float2* out;
     int64_t S2;
@@ -140,7 +142,10 @@ __device__ __forceinline__ void mix_pass(const IO& io, float2* s, int nl, const 
     constexpr int R = MP::radix(P), Ns = MP::ns(P), L = MP::L, S = L / R, NB = MP::NL * S;
     constexpr int T = MP::THREADS, J = (NB + T - 1) / T;
     constexpr bool FIRST = P == 0, LAST = P + 1 == MP::NPASS;
-    constexpr bool LF = IO::LINE_FAST && (FIRST || LAST);  // line index fastest across threads
+    // line index fastest across threads in the first pass (IO::LOAD_LF) or the
+    // last one (IO::STORE_LF); a single pass needs one mapping for both
+    static_assert(MP::NPASS > 1 || IO::LOAD_LF == IO::STORE_LF, "one-pass tiles load and store alike");
+    constexpr bool LF = (FIRST && IO::LOAD_LF) || (LAST && IO::STORE_LF);
     float2 v[J * R];
     int line[J], b[J];
     bool in_tile[J];

@@ -127,6 +127,22 @@ def test_ragged_pow2_templated_stages(torch, monkeypatch, env):
             assert _ragged_check(torch, lengths, data, per_size, d, full_limit=70000) <= TOL_FP32, (env, per_size, d)
 
 
+@pytest.mark.parametrize("env", [{}, {"B300FFT_G_MIXT": "0"}])
+def test_ragged_mixed_fourstep_transposed_rows(torch, monkeypatch, env):
+    """M * 2^k four-steps whose second stage has 64 or 128 points and a row
+    count the fixed 256-thread tile does not divide (5120 = 80 x 64, 6144 =
+    96 x 64, 7168 = 112 x 64, 10240 = 80 x 128, ...): the compile-time
+    transposed-row tile with a partial last tile (or runtime tiles when the
+    compile-time tiles are off).  Every transform compared in full."""
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    lengths = [5120, 6144, 7168, 10240, 14336, 6144, 100, 4099, 20480, 3 * 2 ** 15]
+    data = np.random.default_rng(23).standard_normal(2 * sum(lengths)).astype(np.float32).view(np.complex64)
+    for per_size in (False, True):
+        for d in (-1, +1):
+            assert _ragged_check(torch, lengths, data, per_size, d, full_limit=100000) <= TOL_FP32, (env, per_size, d)
+
+
 def test_ragged_all_lean(torch, monkeypatch):
     """A ragged batch of power-of-two lengths 2^13..2^16 only runs in the lean
     executor alone (one launch)."""
