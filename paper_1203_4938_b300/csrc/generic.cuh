@@ -62,9 +62,13 @@ struct GStage {
                // a power of two),
                // 2000 + 16 M + A: four-step first stage, columns of M * 2^A (compile-time),
                // 3000 + K2: four-step second stage, rows of 2^K2 with the transposed store
+               //            (and the post-multiply of Bluestein's transforms),
+               // 4000 + K: Bluestein's single-tile stage of M = 2^K (pre / post multiplies),
+               // 5000 + A: Bluestein's four-step first stage, columns of 2^A (pre multiply)
     int64_t in_ls, in_es, out_ls, out_es;  // line / element strides (elements)
     int64_t in_valid, out_valid;           // offsets >= these read as 0 / are not stored
     int64_t pre_tab, post_tab;             // table offsets in the pool
+    int64_t mtab;                          // compile-time tiles (tmpl >= 1000): their pass table in the pool
     int64_t lo, hi;                        // four-step two-level table in the pool
     int64_t line_tab;  // >= 0: the lines are separate transforms; line l starts at line_off[line_tab + l]
 };
@@ -394,26 +398,105 @@ __device__ __noinline__ void g_mixed_cols(const float2* gin, float2* gout, int64
 // (row k1 = line0 + l of the [N1][L] work buffer) is read contiguously (b
 // fastest) and its bin e goes to out[k1 + N1 e] (line fastest: runs of up to
 // NL consecutive k1).
+// Optional table multiply of a stage's loads or stores (Bluestein's chirp and
+// filter): v * t[idx] or v * conj(t[idx]) for idx < valid, zero (loads) or
+// nothing (stores) beyond.  t == nullptr: no multiply.
+struct TabMul {
+    const float2* t;
+    int conj;
+    int64_t valid;
+    __device__ __forceinline__ float2 apply(float2 v, int64_t idx) const {
+        if (!t) return v;
+        const float2 w = __ldg(t + idx);
+        return conj ? cmulc(v, w) : cmul(v, w);
+    }
+};
+
 template <int L>
 struct MixRowsT {
     static constexpr bool LOAD_LF = false, STORE_LF = true;
     const float2* in;  // work buffer at row line0
     float2* out;       // output at k1 = line0
-    int64_t n1;
+    int64_t n1, line0;
+    TabMul post;       // bin k = line0 + line + n1 e
     __device__ __forceinline__ float2 load(int line, int e) const { return __ldcg(in + line * L + e); }
-    __device__ __forceinline__ void store(int line, int e, float2 v) const { __stcs(out + line + n1 * e, v); }
+    __device__ __forceinline__ void store(int line, int e, float2 v) const {
+        const int64_t k = line0 + line + n1 * e;
+        if (k < post.valid) __stcs(out + line + n1 * e, post.apply(v, k));
+    }
 };
 
 template <int K2>
 __device__ __noinline__ void g_mixed_rowsT(const float2* gin, float2* gout, int64_t n1, int tile, int inv,
-                                           const float2* __restrict__ tw, float2* smem) {
+                                           const float2* __restrict__ tw, float2* smem, const float2* post_t,
+                                           int post_conj, int64_t post_valid) {
+    const TabMul post{post_t, post_conj, post_valid};
     using MP = MixPlan<1, K2, kGMixLines(1 << K2)>;
     static_assert(MP::SMEM <= kGMixOffF2 * 8, "tile buffer below the line-offset table");
     const int64_t line0 = (int64_t)tile * MP::NL;
     const int nl = (int)(n1 - line0 < MP::NL ? n1 - line0 : MP::NL);
-    const MixRowsT<MP::L> io{gin + line0 * MP::L, gout + line0, n1};
+    const MixRowsT<MP::L> io{gin + line0 * MP::L, gout + line0, n1, line0, post};
     if (inv) mix_pass<MP, 0, true>(io, smem, nl, tw);
     else mix_pass<MP, 0, false>(io, smem, nl, tw);
+}
+
+// Bluestein's single-tile stage: one line of M = 2^K, loads times the pre
+// table (zero beyond pre.valid), stores times the post table (up to post.valid).
+template <int L>
+struct MixLinePP {
+    static constexpr bool LOAD_LF = false, STORE_LF = false;
+    const float2* in;
+    float2* out;
+    TabMul pre, post;
+    __device__ __forceinline__ float2 load(int, int e) const {
+        return e < pre.valid ? pre.apply(__ldcg(in + e), e) : make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void store(int, int e, float2 v) const {
+        if (e < post.valid) __stcg(out + e, post.apply(v, e));
+    }
+};
+
+template <int K>
+__device__ __noinline__ void g_blue_rows(const float2* gin, float2* gout, int inv, const float2* __restrict__ tw,
+                                         float2* smem, const float2* pre_t, int pre_conj, int64_t pre_valid,
+                                         const float2* post_t, int post_conj, int64_t post_valid) {
+    const TabMul pre{pre_t, pre_conj, pre_valid}, post{post_t, post_conj, post_valid};
+    using MP = MixPlan<1, K, 1>;
+    const MixLinePP<MP::L> io{gin, gout, pre, post};
+    if (inv) mix_pass<MP, 0, true>(io, smem, 1, tw);
+    else mix_pass<MP, 0, false>(io, smem, 1, tw);
+}
+
+// Bluestein's four-step first stage: NL adjacent columns of 2^A (stride S2),
+// loads times the pre table (element index col + S2 e, zero beyond
+// pre.valid), stores times the W_M twiddle into the work buffer.
+template <bool INV>
+struct MixColsPre {
+    static constexpr bool LOAD_LF = true, STORE_LF = true;
+    MixCols<INV, true> c;
+    TabMul pre;
+    __device__ __forceinline__ float2 load(int line, int e) const {
+        const int64_t idx = (int64_t)c.col0 + line + c.S2 * e;
+        return idx < pre.valid ? pre.apply(c.load(line, e), idx) : make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void store(int line, int e, float2 v) const { c.store(line, e, v); }
+};
+
+template <int A, int NL>
+__device__ __noinline__ void g_blue_cols(const float2* gin, float2* gout, int64_t S2, int tile, int inv,
+                                         const float2* __restrict__ tw, const float2* __restrict__ lo,
+                                         const float2* __restrict__ hi, int sh, float2* smem, const float2* pre_t,
+                                         int pre_conj, int64_t pre_valid) {
+    const TabMul pre{pre_t, pre_conj, pre_valid};
+    using MP = MixPlan<1, A, NL>;
+    const int64_t col0 = (int64_t)tile * NL;
+    if (inv) {
+        const MixColsPre<true> io{{gin + col0, gout + col0, S2, (uint32_t)col0, lo, hi, sh}, pre};
+        mix_pass<MP, 0, true>(io, smem, NL, tw);
+    } else {
+        const MixColsPre<false> io{{gin + col0, gout + col0, S2, (uint32_t)col0, lo, hi, sh}, pre};
+        mix_pass<MP, 0, false>(io, smem, NL, tw);
+    }
 }
 
 // Compile-time mixed tiles of the stage graph (the lengths of the batched
@@ -430,7 +513,12 @@ __device__ __forceinline__ void g_mixed_tile(const GExecArgs& a, const GTransfor
                                              float2* smem) {
     const float2* gin = g_buf_in(a, x, st.in_buf);
     float2* gout = g_buf_out(a, x, st.out_buf);
-    const float2* tw = a.pool + st.pre_tab;
+    const float2* tw = a.pool + st.mtab;
+    // table multiplies of the loads / stores (Bluestein stages; none elsewhere)
+#define B300_PRE (st.pre != G_PRE_NONE ? a.pool + st.pre_tab : nullptr), (int)(st.pre == G_PRE_TABLE_CONJ), st.in_valid
+#define B300_POST                                                                                           \
+    (st.post == G_POST_TABLE || st.post == G_POST_TABLE_CONJ ? a.pool + st.post_tab : nullptr),            \
+        (int)(st.post == G_POST_TABLE_CONJ), st.out_valid
     switch (st.tmpl) {
 #define B300_R(M, K)                                                                                          \
     case 1000 + 16 * M + K:                                                                                   \
@@ -438,12 +526,25 @@ __device__ __forceinline__ void g_mixed_tile(const GExecArgs& a, const GTransfor
         break;
         B300_G_MIXED_ROWS(B300_R)
 #undef B300_R
-#define B300_T(K2)                                                                        \
-    case 3000 + K2:                                                                       \
-        g_mixed_rowsT<K2>(gin, gout, (int64_t)st.nlines, tile, st.inv, tw, smem);         \
+#define B300_T(K2)                                                                     \
+    case 3000 + K2:                                                                    \
+        g_mixed_rowsT<K2>(gin, gout, (int64_t)st.nlines, tile, st.inv, tw, smem, B300_POST); \
         break;
         B300_T(5) B300_T(6) B300_T(7) B300_T(8) B300_T(9) B300_T(10) B300_T(11) B300_T(12)
 #undef B300_T
+#define B300_B(K)                                                  \
+    case 4000 + K:                                                 \
+        g_blue_rows<K>(gin, gout, st.inv, tw, smem, B300_PRE, B300_POST); \
+        break;
+        B300_B(7) B300_B(8) B300_B(9) B300_B(10) B300_B(11) B300_B(12)
+#undef B300_B
+#define B300_BC(A, NL)                                                                                           \
+    case 5000 + A:                                                                                               \
+        g_blue_cols<A, NL>(gin, gout, st.in_es, tile, st.inv, tw, a.pool + st.lo, a.pool + st.hi, st.sh, smem,     \
+                           B300_PRE);                                                                            \
+        break;
+        B300_BC(6, 64) B300_BC(7, 32) B300_BC(8, 16) B300_BC(9, 8)
+#undef B300_BC
 #define B300_C(M, A, NL)                                                                                          \
     case 2000 + 16 * M + A:                                                                                       \
         g_mixed_cols<M, A, NL>(gin, gout, st.in_es, tile, st.inv, tw, a.pool + st.lo, a.pool + st.hi, st.sh, smem); \
@@ -453,6 +554,8 @@ __device__ __forceinline__ void g_mixed_tile(const GExecArgs& a, const GTransfor
         default:
             break;
     }
+#undef B300_PRE
+#undef B300_POST
 }
 
 template <bool MIX>

@@ -279,7 +279,7 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
                 s.tmpl = 1000 + 16 * mm + kk;
                 s.lpt = std::min(kGMixLines((int)n), std::max(1, (int)lines));
                 s.ntiles = (int)((lines + kGMixLines((int)n) - 1) / kGMixLines((int)n));
-                s.pre_tab = B.mixed_table(mm, kk);
+                s.mtab = B.mixed_table(mm, kk);
             }
             (d ? i : f).push_back(s);
         }
@@ -339,7 +339,7 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
                 a.tmpl = 2000 + 16 * mm + aa;
                 a.lpt = width;
                 a.ntiles = (int)(n2 / width);
-                a.pre_tab = B.mixed_table(mm, aa);
+                a.mtab = B.mixed_table(mm, aa);
             }
             GStage b = base_stage(sb, (int)n1, lines_per_tile((int)n2, cfg.lpt_b), d);
             b.in_buf = G_BUF_W1;
@@ -364,7 +364,7 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
                 // (any line count; the last tile may hold fewer lines)
                 b.tmpl = 3000 + l2;
                 b.ntiles = (int)((n1 + kGMixLines((int)n2) - 1) / kGMixLines((int)n2));
-                b.pre_tab = B.mixed_table(1, l2);
+                b.mtab = B.mixed_table(1, l2);
             }
             (d ? i : f).push_back(a);
             (d ? i : f).push_back(b);
@@ -397,6 +397,12 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
                 b.out_valid = n;
                 b.post = d ? G_POST_TABLE_CONJ : G_POST_TABLE;
                 b.post_tab = bt[0];
+                int lm = 0;
+                while ((int64_t(1) << lm) < M) ++lm;
+                if (lm >= 7 && lm <= 12 && env_i("B300FFT_G_MIXT", 1) != 0) {  // compile-time tiles
+                    a.tmpl = b.tmpl = 4000 + lm;
+                    a.mtab = b.mtab = B.mixed_table(1, lm);
+                }
                 (d ? i : f).push_back(a);
                 (d ? i : f).push_back(b);
             }
@@ -441,6 +447,21 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
                     } else {
                         b.post = d ? G_POST_TABLE_CONJ : G_POST_TABLE;
                         b.post_tab = bt[0];
+                    }
+                    // compile-time tiles: columns of 2^la (pre multiply, W_M twiddle),
+                    // then rows of 2^lb with the transposed store (post multiply)
+                    int la = 0, lb = 0;
+                    while ((int64_t(1) << la) < m1) ++la;
+                    while ((int64_t(1) << lb) < m2) ++lb;
+                    const int cw = la >= 6 && la <= 9 ? (4096 >> la < 64 ? 4096 >> la : 64) : 0;
+                    if (cw && m2 % cw == 0 && lb >= 5 && lb <= 12 && env_i("B300FFT_G_MIXT", 1) != 0) {
+                        a.tmpl = 5000 + la;
+                        a.mtab = B.mixed_table(1, la);
+                        a.lpt = cw;
+                        a.ntiles = (int)(m2 / cw);
+                        b.tmpl = 3000 + lb;
+                        b.mtab = B.mixed_table(1, lb);
+                        b.ntiles = (int)((m1 + kGMixLines((int)m2) - 1) / kGMixLines((int)m2));
                     }
                     (d ? i : f).push_back(a);
                     (d ? i : f).push_back(b);
