@@ -784,26 +784,20 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
 
     // Persistent-launch order: transforms in the same (largest kind first)
     // order, stage s of a transform placed `lag` items after its stage s-1,
-    // so every dependency precedes its consumers in the queue.  A short lag
-    // reads intermediates back from L2 but makes later stages wait; measured,
-    // it pays only for one length run as a four-step (2 x 3 x SMs items:
-    // 65536-point transforms 140 vs 147 us per 2^24 elements).  Everything
-    // else -- the ragged mix (1.21 vs 1.31 ms), Bluestein (1009: 1025 vs
-    // 1116 us) -- runs every transform's first stage before any second
-    // stage (an unlimited lag).
+    // so every dependency precedes its consumers in the queue.  A four-step
+    // transform's second stage follows its first 5 x SMs items later (about
+    // the CTAs in flight: the intermediate is read back from L2, and the
+    // first stage is done by then): ragged mix 0.910 -> 0.845 ms against an
+    // unlimited lag (1 x SMs: 1.24 ms, 2 x SMs: 0.93, 8 x SMs: 0.875).  Other
+    // multi-stage transforms (Bluestein's chains) run every first stage before
+    // any second one (an unlimited lag): Bluestein 1009 1025 vs 1116 us with
+    // a short lag.
     std::vector<uint64_t> items_lag;
     {
         int dev0 = 0, sms0 = 148;
         cudaGetDevice(&dev0);
         cudaDeviceGetAttribute(&sms0, cudaDevAttrMultiProcessorCount, dev0);
-        bool one_fourstep = uniq.size() == 1;
-        if (one_fourstep) {
-            const Kind& k = kinds[uniq[0]];
-            const GStage& a0 = B.st_f[k.first];
-            one_fourstep = k.nstages == 2 && (a0.post == G_POST_TW4 || a0.tmpl >= 2000 ||
-                                              (a0.tmpl > 0 && a0.tmpl < 100 && (a0.tmpl & 1) == 0));
-        }
-        const int64_t lag = env_i("B300FFT_G_LAG", one_fourstep ? 2 * 3 * sms0 : (1 << 30));
+        const int64_t lag_fs = env_i("B300FFT_G_LAG", 5 * sms0);
         struct Grp {
             int64_t key;
             int s, t, ntiles;
@@ -812,6 +806,10 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
         int64_t k0 = 0;
         for (size_t ki = 0; ki < uniq.size(); ++ki) {
             const Kind& k = kinds[uniq[ki]];
+            const GStage& a0 = B.st_f[k.first];
+            const bool fourstep = k.nstages == 2 && (a0.post == G_POST_TW4 || (a0.tmpl >= 2000 && a0.tmpl < 3000) ||
+                                                     (a0.tmpl > 0 && a0.tmpl < 100 && (a0.tmpl & 1) == 0));
+            const int64_t lag = fourstep ? lag_fs : (int64_t(1) << 30);
             for (int t : by_kind[ki]) {
                 int64_t key = k0;
                 for (int s2 = 0; s2 < k.nstages; ++s2) {
