@@ -184,25 +184,74 @@ def oracle_sample(budget_elems: int = 1 << 21, sizes=None, threads: int = 0):
     return fl / secs / 1e9, secs, threads, desc
 
 
+def sweep_config(args, world: int) -> dict:
+    """The sweep's `config` object (shared by both arms)."""
+    return {"workload": f"sweep N=2^{args.lo}..2^{args.hi}, 2^{TOTAL_LOG2} complex64/size"
+                        f"{' (quick: 1/16 batch)' if args.quick else ''}, fwd+inv, normal(0,1) seed 1",
+            "l2": "inputs (512 MiB per size) larger than L2; no flush", "parallelism": f"replicas{world}"}
+
+
+def reference_budget(steps: int) -> int:
+    """Elements per size and step of the reference arm, so that warm-up plus
+    timed steps take a few minutes on the host cores in total."""
+    if steps <= 8:
+        return 1 << 21
+    if steps <= 24:
+        return 1 << 19
+    return 1 << 17
+
+
+def oracle_step(step: int, budget: int, threads: int, sizes):
+    """One reference-arm step: forward + inverse of min(batch, budget/N)
+    transforms of every sweep size N <= budget, plus one transform of one
+    larger size, taken in turn (step mod their count).  Returns (flops, s)."""
+    import oracle
+    small = [t for t in sizes if t[1] <= budget]
+    large = [t for t in sizes if t[1] > budget]
+    pick = small + ([large[step % len(large)]] if large else [])
+    fl, secs = 0.0, 0.0
+    for k, n, b in pick:
+        m = max(1, min(b, budget // n))
+        x = inputs.normal_batch(m, n, seed=1)
+        t0 = time.perf_counter()
+        y = oracle.fft(x, -1, threads)
+        oracle.fft(y, +1, threads)
+        secs += time.perf_counter() - t0
+        fl += 2 * 5.0 * n * k * m
+    return fl, secs
+
+
 def run_reference(args):
+    """The FP64 oracle on the host cores, on this benchmark's metric and
+    config: W untimed steps, then K timed ones; value = flops / seconds over
+    the timed steps.  Rank 0 only."""
+    import oracle
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
-    for _ in range(args.warmup if args.warmup else 0):
-        pass
-    vals, secs_total = [], 0.0
-    gf = None
-    for _ in range(max(1, args.steps)):
-        gf, secs, threads, desc = oracle_sample(1 << 19 if args.quick else 1 << 21)
-        vals.append(gf)
-        secs_total += secs
-    value = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs_total / max(1, args.steps),
+    threads = oracle.num_cpus()
+    sizes = inputs.sweep_sizes(TOTAL_LOG2, args.lo, args.hi)
+    steps = max(1, args.steps)
+    budget = reference_budget(steps + max(0, args.warmup))
+    if args.quick:
+        budget = min(budget, 1 << 17)
+    for w in range(max(0, args.warmup)):
+        oracle_step(w, budget, threads, sizes)
+    fl, secs = 0.0, 0.0
+    for i in range(steps):
+        f, s = oracle_step(args.warmup + i, budget, threads, sizes)
+        fl += f
+        secs += s
+    value = fl / secs / 1e9
+    nlarge = sum(1 for t in sizes if t[1] > budget)
+    desc = (f"FP64 C oracle (radix-2) on {threads} threads; per step fwd+inv of min(batch, 2^{budget.bit_length() - 1}"
+            f"/N) transforms of each size N<=2^{budget.bit_length() - 1}"
+            + (f", plus one transform of one of the {nlarge} larger sizes in turn" if nlarge else ""))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "sweep 2^10..2^24 x 2^26 elems (bounded CPU sample)"},
-            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-                             "sample": desc},
+            "data": "synthetic", "config": sweep_config(args, world),
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -422,9 +471,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"sweep N=2^{args.lo}..2^{args.hi}, 2^{TOTAL_LOG2} complex64/size"
-                                   f"{' (quick: 1/16 batch)' if args.quick else ''}, fwd+inv, normal(0,1) seed 1",
-                       "l2": "inputs (512 MiB per size) larger than L2; no flush", "parallelism": f"replicas{world}"},
+            "config": sweep_config(args, world),
             "gpu_launches": args.steps * len(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu)",
