@@ -86,7 +86,12 @@ enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
  *   precision one of fft_precision (tensor-core modes: 1-D, N = 16^k, k >= 2).
  * Computes the twiddle tables on the device in FP64 and rounds them once to
  * FP32; allocates the workspace a multi-pass length needs.  Synchronises the
- * current device once.  Returns NULL on error; fft_last_error() says why. */
+ * current device once.  2-D: sides that are powers of two (W <= 2^14,
+ * H <= 2^12) or 3/5/7 * 2^k <= 4096 run as a rows pass and an in-place column
+ * pass; any other pair of lengths that a 1-D plan supports runs as a 1-D plan
+ * over the rows, a transpose, a 1-D plan over the columns and a transpose
+ * back (a batch*H*W complex workspace).  Returns NULL on error;
+ * fft_last_error() says why. */
 FFT_API fft_plan fft_plan_create(int dims, const int64_t *lengths, int64_t batch, int precision);
 
 /* Create a plan for `count` 1-D transforms of uneven lengths, packed back to
@@ -174,14 +179,17 @@ FFT_API fft_status fft_exec(fft_plan plan, const void *in, void *out, int direct
  * form is compared against.  For other plans it is fft_exec. */
 FFT_API fft_status fft_exec_per_size(fft_plan plan, const void *in, void *out, int direction, void *stream);
 
-/* Read and clear the plan's device status word (synchronous; call it after
- * the stream that ran fft_exec has been synchronised). */
+/* Read and clear the plan's device status word, and those of the plans a
+ * real or transposing 2-D plan runs inside it; returns the first nonzero one
+ * (synchronous; call it after the stream that ran fft_exec has been
+ * synchronised). */
 FFT_API fft_status fft_plan_check(fft_plan plan);
 
 /* Free every resource of the plan.  Synchronises the device first. */
 FFT_API fft_status fft_plan_destroy(fft_plan plan);
 
-/* Bytes of device workspace the plan holds (0 for single-pass plans). */
+/* Bytes of device workspace the plan holds, with those of the plans it runs
+ * inside it (0 for single-pass plans). */
 FFT_API size_t fft_plan_workspace_bytes(fft_plan plan);
 
 /* Static English text for a status value. */

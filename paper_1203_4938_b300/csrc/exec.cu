@@ -147,6 +147,20 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
         case PlanKind::Real:
             if (!want(0)) return FFT_OK;
             return exec_real(p, in, out, inv, st);
+        case PlanKind::TwoDTranspose: {
+            // kernel sequence: the rows plan's, transpose, the columns plan's, transpose
+            const int64_t h = p->len[0], w = p->len[1];
+            const int ka = p->inner->kernels, kb = p->inner2->kernels;
+            fft_status s = FFT_OK;
+            if (only < 0 || only < ka) s = exec_plan(p->inner, in, out, inv, st, only < 0 ? -1 : only, per_size);
+            if (s == FFT_OK && want(ka)) e = launch_transpose(out, p->d_work, h, w, p->batch, st);
+            if (s == FFT_OK && e == cudaSuccess && (only < 0 || (only > ka && only <= ka + kb)))
+                s = exec_plan(p->inner2, p->d_work, p->d_work, inv, st, only < 0 ? -1 : only - ka - 1, per_size);
+            if (s == FFT_OK && e == cudaSuccess && want(ka + kb + 1))
+                e = launch_transpose(p->d_work, out, w, h, p->batch, st);
+            if (s != FFT_OK) return s;
+            break;
+        }
         case PlanKind::TensorCore:
             return exec_tc(p, in, out, inv, st, only);
         case PlanKind::Generic:

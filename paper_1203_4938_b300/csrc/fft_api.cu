@@ -71,6 +71,10 @@ void destroy_plan_resources(fft_plan_s* p) {
         fft_plan_destroy(p->inner);
         p->inner = nullptr;
     }
+    if (p->inner2) {
+        fft_plan_destroy(p->inner2);
+        p->inner2 = nullptr;
+    }
     if (p->gplan) {
         graph_plan_free(p->gplan);
         delete p->gplan;
@@ -614,6 +618,33 @@ fft_status build_mixed_2d(fft_plan_s* p, int64_t h, int64_t w) {
     return FFT_OK;
 }
 
+// Any other H x W: the 2-D DFT as 1-D DFTs along the rows, then along the
+// columns, with the column pass done on transposed data: a 1-D plan over the
+// batch * H rows of length W (in -> out), a transpose (out -> workspace), a
+// 1-D plan over the batch * W rows of length H (in place in the workspace) and
+// a transpose back (workspace -> out).  Each 1-D plan is whatever
+// fft_plan_create picks for its length (power of two, mixed radix,
+// Bluestein), so every pair of supported 1-D lengths works in 2-D.
+fft_status build_2d_transpose(fft_plan_s* p, int64_t h, int64_t w) {
+    if (env_int("B300FFT_2D_TRANSPOSE", 1) == 0) return FFT_ERR_UNSUPPORTED;
+    if (p->d_tables || p->d_work || p->d_aux || p->gplan) return FFT_ERR_UNSUPPORTED;  // a partly built plan
+    const int64_t lw = w, lh = h;
+    p->inner = fft_plan_create(1, &lw, p->batch * h, FFT_FP32);
+    if (!p->inner) return fft_last_error();
+    p->inner2 = fft_plan_create(1, &lh, p->batch * w, FFT_FP32);
+    if (!p->inner2) return fft_last_error();
+    p->work_bytes = (size_t)h * (size_t)w * (size_t)p->batch * sizeof(float2);
+    if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
+    p->kind = PlanKind::TwoDTranspose;
+    p->kernels = fft_plan_kernel_count(p->inner) + 1 + fft_plan_kernel_count(p->inner2) + 1;
+    char a[110], b[110];
+    fft_plan_describe(p->inner, a, sizeof a);
+    fft_plan_describe(p->inner2, b, sizeof b);
+    std::snprintf(p->desc, sizeof p->desc, "2d-transpose H=%lld W=%lld: rows [%s], transpose, columns [%s], transpose",
+                  (long long)h, (long long)w, a, b);
+    return FFT_OK;
+}
+
 // Non-power-of-two 1-D lengths: mixed radix 2/3/4/5/7/8/16 (single tile or
 // four-step) or Bluestein, through the stage-graph executor.
 fft_status build_generic_1d(fft_plan_s* p) {
@@ -683,9 +714,11 @@ fft_plan fft_plan_create(int dims, const int64_t* lengths, int64_t batch, int pr
         }
     } else {
         const int lh = ilog2_exact(lengths[0]), lw = ilog2_exact(lengths[1]);
-        if (lh >= 0 && lw >= 0) s = build_pow2_2d(p, lh, lw);
+        if (env_int("B300FFT_2D_TRANSPOSE", 1) == 2) s = build_2d_transpose(p, lengths[0], lengths[1]);  // forced
+        else if (lh >= 0 && lw >= 0) s = build_pow2_2d(p, lh, lw);
         else if (env_int("B300FFT_MIXED", 1) != 0) s = build_mixed_2d(p, lengths[0], lengths[1]);
         else s = FFT_ERR_UNSUPPORTED;
+        if (s == FFT_ERR_UNSUPPORTED) s = build_2d_transpose(p, lengths[0], lengths[1]);
     }
     if (s != FFT_OK) return fail(s, p);
     return finish(p);
@@ -797,9 +830,15 @@ fft_status fft_plan_check(fft_plan plan) {
     if (h != 0) {
         int z = 0;
         cudaMemcpy(plan->d_status, &z, sizeof(int), cudaMemcpyHostToDevice);
-        return (fft_status)h;
     }
-    return FFT_OK;
+    // the plans a Real or TwoDTranspose plan runs (their words are read and cleared too)
+    fft_status r = (fft_status)h;
+    for (fft_plan q : {plan->inner, plan->inner2}) {
+        if (!q) continue;
+        const fft_status s = fft_plan_check(q);
+        if (r == FFT_OK) r = s;
+    }
+    return r;
 }
 
 fft_status fft_plan_destroy(fft_plan plan) {
@@ -817,7 +856,10 @@ fft_status fft_plan_destroy(fft_plan plan) {
 
 size_t fft_plan_workspace_bytes(fft_plan plan) {
     if (!is_registered(plan)) return 0;
-    return plan->work_bytes;
+    size_t b = plan->work_bytes;
+    for (fft_plan q : {plan->inner, plan->inner2})
+        if (q) b += fft_plan_workspace_bytes(q);
+    return b;
 }
 
 const char* fft_status_string(fft_status s) {

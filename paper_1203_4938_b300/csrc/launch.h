@@ -42,6 +42,10 @@ cudaError_t launch_rows_mixed(int m, int k, bool inv, const float2* in, float2* 
 // `items` row-major [M * 2^a][S2] arrays, mixed_cols_width(m, a) columns per
 // CTA (0: no kernel for that length), times W_N^{n2 k1} from (lo, hi, sh).
 int mixed_cols_width(int m, int a);
+// out[b][c][r] = in[b][r][c] for [batch][rows][cols] complex64 (transpose.cu);
+// in != out.
+cudaError_t launch_transpose(const float2* in, float2* out, int64_t rows, int64_t cols, int64_t batch,
+                             cudaStream_t st);
 // 2-D column pass: columns of length M * 2^K (no twiddle), mixed_cols2d_width
 // columns per CTA (S2 must be a multiple of it).
 int mixed_cols2d_width(int m, int k);

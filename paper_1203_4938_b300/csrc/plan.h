@@ -21,6 +21,7 @@ enum class PlanKind : int {
     RowsMixed, // single-pass mixed-radix rows kernel, L = M * 2^K <= 4096 (M = 3, 5, 7)
     FourStepMixed, // N = (M * 2^a) * 2^b: mixed columns kernel + power-of-two transposed rows
     TwoDMixed, // 2-D with a side of M * 2^K: rows kernel (power of two or mixed), then in-place column pass
+    TwoDTranspose,  // any other 2-D: 1-D plan over the rows, transpose, 1-D plan over the columns, transpose
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
     Ragged,    // persistent work-queue kernel over uneven lengths
@@ -46,8 +47,8 @@ struct fft_plan_s {
     // power-of-two kernels
     int logn_a = 0, logn_b = 0, sh = 0;
     int mix_m = 0;  // RowsMixed: L = mix_m * 2^logn_a
-    int mix_mh = 0, mix_mw = 0;
-    bool real_fused = false;  // Real: one-pass fused rows + split kernel (h = 2^5 .. 2^12)  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
+    int mix_mh = 0, mix_mw = 0;  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
+    bool real_fused = false;     // Real: one-pass fused rows + split kernel (h = 2^5 .. 2^12)
     int cols_c = 0;     // columns kernel width
     int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA
 
@@ -71,7 +72,8 @@ struct fft_plan_s {
     cudaGraphExec_t graph_exec = nullptr;
 
     b300fft::GraphPlan* gplan = nullptr;  // Generic / Ragged kinds
-    fft_plan inner = nullptr;             // Real kind: the complex plan of N/2
+    fft_plan inner = nullptr;             // Real: the complex plan of N/2; TwoDTranspose: the rows plan
+    fft_plan inner2 = nullptr;            // TwoDTranspose: the plan over the transposed columns
     b300fft::TcPlan* tc = nullptr;
 
     int kernels = 0;

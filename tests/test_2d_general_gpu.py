@@ -1,0 +1,105 @@
+"""Parity of the general 2-D plan (1-D plan over the rows, transpose, 1-D
+plan over the transposed columns, transpose back) with the FP64 oracle's 2-D
+DFT: sides the in-place column kernels do not cover (any length the 1-D path
+supports, including primes and powers of two above 4096), in place, the
+kernel-by-kernel sequence, and the status words of the inner plans.
+Bar: per-image relative L2 error <= 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_4938_b300 import fft as F
+from tests.gpu_util import TOL_FP32, cuda_or_skip, max_rel_l2, run, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(7, 5, 3), (9, 64, 2), (64, 11, 2), (97, 1009, 1), (1080, 1920, 1), (1000, 1000, 1), (8192, 512, 1),
+          (16384, 64, 2), (3, 6000, 2), (6000, 3, 2), (1, 77, 4), (77, 1, 4)]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+def image(h, w, batch, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((batch, h, w)) + 1j * rng.standard_normal((batch, h, w))).astype(np.complex64)
+
+
+@pytest.mark.parametrize("h,w,batch", SHAPES)
+def test_general_2d(torch, h, w, batch):
+    x = image(h, w, batch, h * 31 + w)
+    with F.Plan((h, w), batch) as p:
+        assert p.describe().startswith("2d-transpose"), p.describe()
+    for d in (-1, +1):
+        y = run((h, w), batch, x, d)
+        ref = oracle.fft2(x, d)
+        assert max_rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1), -1) <= TOL_FP32, (h, w, d)
+
+
+@pytest.mark.parametrize("h,w", [(1000, 1000), (8192, 512)])
+def test_general_2d_in_place_round_trip(torch, h, w):
+    x = image(h, w, 1, 5)
+    y = run((h, w), 1, x, -1, inplace=True)
+    assert max_rel_l2(y.reshape(1, -1), oracle.fft2(x, -1).reshape(1, -1), -1) <= TOL_FP32
+    z = run((h, w), 1, y.astype(np.complex64), +1, inplace=True) / (h * w)
+    assert max_rel_l2(z.reshape(1, -1), x.reshape(1, -1), -1) <= 2 * TOL_FP32
+
+
+def test_general_2d_kernel_sequence(torch):
+    # fft_exec_kernel k = 0 .. count-1 in order equals one fft_exec
+    h, w, batch = 96, 1009, 2
+    x = to_dev(image(h, w, batch, 8))
+    with F.Plan((h, w), batch) as p:
+        n = F.fft_plan_kernel_count(p.handle)
+        assert n >= 4, n
+        full = p.forward(x).clone()
+        out = torch.empty_like(x)
+        for k in range(n):
+            p.exec_kernel(k, x, out, F.FFT_FORWARD)
+        torch.cuda.synchronize()
+        p.check()
+        assert torch.equal(out, full)
+
+
+def test_general_2d_switched_off(torch, monkeypatch):
+    monkeypatch.setenv("B300FFT_2D_TRANSPOSE", "0")
+    assert F.fft_plan_create(2, [7, 5], 1, 0) is None
+    assert F.fft_last_error() == F.FFT_ERR_UNSUPPORTED
+
+
+def test_inner_plan_timeout_reaches_outer_check(torch, monkeypatch):
+    """A bounded wait that expires inside the column plan (a persistent
+    four-step over H = 2^16, one chunk withheld) is reported by
+    fft_plan_check on the 2-D plan, and the words are cleared."""
+    h, w, batch = 1 << 16, 3, 1
+    x = to_dev(image(h, w, batch, 2))
+    monkeypatch.setenv("B300FFT_DEBUG_WITHHOLD_CHUNK", "0")
+    monkeypatch.setenv("B300FFT_SPIN_LIMIT", "20000")
+    monkeypatch.setenv("B300FFT_CHUNK_MB", "1")
+    with F.Plan((h, w), batch) as p:
+        assert "persist" in p.describe(), p.describe()
+        p.forward(x)
+        torch.cuda.synchronize()
+        assert F.fft_plan_check(p.handle) == F.FFT_ERR_TIMEOUT
+        assert F.fft_plan_check(p.handle) == F.FFT_OK
+
+
+def test_real_plan_reports_inner_timeout(torch, monkeypatch):
+    # the same for a real plan whose complex plan of N/2 = 2^16 times out
+    n, batch = 1 << 17, 2
+    x = torch.randn(batch, n, device="cuda")
+    monkeypatch.setenv("B300FFT_DEBUG_WITHHOLD_CHUNK", "0")
+    monkeypatch.setenv("B300FFT_SPIN_LIMIT", "20000")
+    monkeypatch.setenv("B300FFT_CHUNK_MB", "1")
+    h = F.fft_plan_create_real(n, batch)
+    assert h is not None
+    try:
+        out = torch.empty(batch, n // 2 + 1, dtype=torch.complex64, device="cuda")
+        assert F.fft_exec(h, x.data_ptr(), out.data_ptr(), F.FFT_FORWARD) == F.FFT_OK
+        torch.cuda.synchronize()
+        assert F.fft_plan_check(h) == F.FFT_ERR_TIMEOUT
+        assert F.fft_plan_check(h) == F.FFT_OK
+    finally:
+        F.fft_plan_destroy(h)

@@ -133,8 +133,12 @@ def test_2d_mixed_in_place(torch):
 
 
 @pytest.mark.parametrize("h,w", [(7, 5), (9, 64), (64, 11)])
-def test_2d_unsupported_sides(torch, h, w):
+def test_2d_sides_outside_the_column_kernels(torch, monkeypatch, h, w):
     # 7 x 5: a 7-point column tile holds 32 columns and 5 is not a multiple;
-    # 9 and 11 are not M * 2^K: no 2-D plan, FFT_ERR_UNSUPPORTED
+    # 9 and 11 are not M * 2^K: no in-place 2-D plan, so the general
+    # (transposing) plan takes them, and without it FFT_ERR_UNSUPPORTED
+    with F.Plan((h, w), 1) as p:
+        assert p.describe().startswith("2d-transpose"), p.describe()
+    monkeypatch.setenv("B300FFT_2D_TRANSPOSE", "0")
     assert F.fft_plan_create(2, [h, w], 1, 0) is None
     assert F.fft_last_error() == F.FFT_ERR_UNSUPPORTED
