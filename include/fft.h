@@ -90,7 +90,10 @@ enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
  * H <= 2^12) or 3/5/7 * 2^k <= 4096 run as a rows pass and an in-place column
  * pass; any other pair of lengths that a 1-D plan supports runs as a 1-D plan
  * over the rows, a transpose, a 1-D plan over the columns and a transpose
- * back (a batch*H*W complex workspace).  Returns NULL on error;
+ * back (a batch*H*W complex workspace).  1-D lengths above 2^24 points
+ * that factor as N1 * N2 with both factors supported run as a six-step
+ * (transpose, N1-point plan, twiddle + transpose, N2-point plan, transpose;
+ * a batch*N complex workspace).  Returns NULL on error;
  * fft_last_error() says why. */
 FFT_API fft_plan fft_plan_create(int dims, const int64_t *lengths, int64_t batch, int precision);
 

@@ -147,6 +147,35 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
         case PlanKind::Real:
             if (!want(0)) return FFT_OK;
             return exec_real(p, in, out, inv, st);
+        case PlanKind::SixStep: {
+            // kernel sequence: transpose, the N1 plan's, twiddle-transpose, the N2 plan's, transpose
+            const int64_t n1 = p->six_n1, n2 = p->six_n2, n = n1 * n2;
+            const int ka = p->inner->kernels, kb = p->inner2->kernels;
+            const bool inplace = in == out;
+            float2* t = inplace ? p->d_work : out;  // [N2][N1] between the first two steps
+            float2* z = inplace ? out : p->d_work;  // [N1][N2] between the last two
+            fft_status s = FFT_OK;
+            if (want(0)) e = launch_transpose(in, t, n1, n2, p->batch, st);
+            if (e == cudaSuccess && (only < 0 || (only >= 1 && only <= ka)))
+                s = exec_plan(p->inner, t, t, inv, st, only < 0 ? -1 : only - 1, per_size);
+            if (s == FFT_OK && e == cudaSuccess && want(ka + 1))
+                e = launch_twiddle_transpose(t, z, n2, n1, p->batch, n, p->d_tables + p->off_lo,
+                                             p->d_tables + p->off_hi, p->sh, inv, st);
+            if (s == FFT_OK && e == cudaSuccess && (only < 0 || (only >= ka + 2 && only <= ka + 1 + kb)))
+                s = exec_plan(p->inner2, z, z, inv, st, only < 0 ? -1 : only - ka - 2, per_size);
+            if (s == FFT_OK && e == cudaSuccess && want(ka + kb + 2)) {
+                if (inplace) {
+                    e = launch_transpose(z, p->d_work, n1, n2, p->batch, st);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(out, p->d_work, (size_t)n * (size_t)p->batch * sizeof(float2),
+                                            cudaMemcpyDeviceToDevice, st);
+                } else {
+                    e = launch_transpose(z, out, n1, n2, p->batch, st);
+                }
+            }
+            if (s != FFT_OK) return s;
+            break;
+        }
         case PlanKind::TwoDTranspose: {
             // kernel sequence: the rows plan's, transpose, the columns plan's, transpose
             const int64_t h = p->len[0], w = p->len[1];

@@ -645,6 +645,65 @@ fft_status build_2d_transpose(fft_plan_s* p, int64_t h, int64_t w) {
     return FFT_OK;
 }
 
+// 1-D lengths above what one plan covers (2^24 points): the six-step form of
+// N = N1 * N2 (Sec. III-A's split into DFTs of the factors) with N1 <= N2
+// the divisor nearest sqrt(N) whose two lengths both have 1-D plans:
+// transpose [N1][N2] -> [N2][N1], N1-point plan over batch * N2 rows, multiply
+// by W_N^(n2*k1) while transposing back to [N1][N2], N2-point plan over
+// batch * N1 rows, transpose to [N2][N1], which is X[k1 + N1 * k2] in natural
+// order.  Every pass is a batched plan of its own (power of two, mixed radix,
+// Bluestein); the twiddle comes from two FP64-generated tables of W_N.
+fft_status build_sixstep(fft_plan_s* p, int64_t n) {
+    if (env_int("B300FFT_SIXSTEP", 1) == 0 || n <= (int64_t(1) << 24) || n >= (int64_t(1) << 31))
+        return FFT_ERR_UNSUPPORTED;
+    if (p->gplan) {  // a stage-graph plan that did not take the length
+        graph_plan_free(p->gplan);
+        delete p->gplan;
+        p->gplan = nullptr;
+    }
+    if (p->d_tables || p->d_work || p->d_aux) return FFT_ERR_UNSUPPORTED;
+    int64_t root = 1;
+    while ((root + 1) * (root + 1) <= n) ++root;
+    int tries = 0;
+    for (int64_t d = root; d >= 2 && tries < 8; --d) {
+        if (n % d != 0 || n / d > (int64_t(1) << 24)) continue;
+        ++tries;
+        const int64_t n1 = d, n2 = n / d;
+        fft_plan a = fft_plan_create(1, &n1, p->batch * n2, FFT_FP32);
+        if (!a) continue;
+        fft_plan b = fft_plan_create(1, &n2, p->batch * n1, FFT_FP32);
+        if (!b) {
+            fft_plan_destroy(a);
+            continue;
+        }
+        p->inner = a;
+        p->inner2 = b;
+        p->six_n1 = n1;
+        p->six_n2 = n2;
+        int lg = 0;
+        while ((int64_t(1) << lg) < n) ++lg;
+        p->sh = (lg + 1) / 2;
+        const int64_t elo = int64_t(1) << p->sh, ehi = (n + elo - 1) / elo;
+        p->off_lo = 0;
+        p->off_hi = (size_t)elo;
+        fft_status s = alloc_tables(p, (size_t)(elo + ehi));
+        if (s != FFT_OK) return s;
+        if (gen_root_table(p->d_tables + p->off_lo, elo, 1, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+        if (gen_root_table(p->d_tables + p->off_hi, ehi, elo, n, 0) != cudaSuccess) return FFT_ERR_CUDA;
+        p->work_bytes = (size_t)n * (size_t)p->batch * sizeof(float2);
+        if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
+        p->kind = PlanKind::SixStep;
+        p->kernels = fft_plan_kernel_count(a) + fft_plan_kernel_count(b) + 3;
+        char da[100], db[100];
+        fft_plan_describe(a, da, sizeof da);
+        fft_plan_describe(b, db, sizeof db);
+        std::snprintf(p->desc, sizeof p->desc, "sixstep N=%lld = %lld x %lld: [%s], twiddle-transpose, [%s]",
+                      (long long)n, (long long)n1, (long long)n2, da, db);
+        return FFT_OK;
+    }
+    return FFT_ERR_UNSUPPORTED;
+}
+
 // Non-power-of-two 1-D lengths: mixed radix 2/3/4/5/7/8/16 (single tile or
 // four-step) or Bluestein, through the stage-graph executor.
 fft_status build_generic_1d(fft_plan_s* p) {
@@ -712,6 +771,7 @@ fft_plan fft_plan_create(int dims, const int64_t* lengths, int64_t batch, int pr
         } else {
             s = build_generic_1d(p);
         }
+        if (s == FFT_ERR_UNSUPPORTED) s = build_sixstep(p, lengths[0]);
     } else {
         const int lh = ilog2_exact(lengths[0]), lw = ilog2_exact(lengths[1]);
         if (env_int("B300FFT_2D_TRANSPOSE", 1) == 2) s = build_2d_transpose(p, lengths[0], lengths[1]);  // forced

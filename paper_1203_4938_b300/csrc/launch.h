@@ -46,6 +46,11 @@ int mixed_cols_width(int m, int a);
 // in != out.
 cudaError_t launch_transpose(const float2* in, float2* out, int64_t rows, int64_t cols, int64_t batch,
                              cudaStream_t st);
+// out[b][c][r] = in[b][r][c] * W_n^{r*c} (conjugated when inv); lo / hi: the
+// two-level root tables of n (2^sh and ceil(n / 2^sh) entries); in != out.
+cudaError_t launch_twiddle_transpose(const float2* in, float2* out, int64_t rows, int64_t cols, int64_t batch,
+                                     int64_t n, const float2* lo, const float2* hi, int sh, bool inv,
+                                     cudaStream_t st);
 // 2-D column pass: columns of length M * 2^K (no twiddle), mixed_cols2d_width
 // columns per CTA (S2 must be a multiple of it).
 int mixed_cols2d_width(int m, int k);

@@ -22,6 +22,7 @@ enum class PlanKind : int {
     FourStepMixed, // N = (M * 2^a) * 2^b: mixed columns kernel + power-of-two transposed rows
     TwoDMixed, // 2-D with a side of M * 2^K: rows kernel (power of two or mixed), then in-place column pass
     TwoDTranspose,  // any other 2-D: 1-D plan over the rows, transpose, 1-D plan over the columns, transpose
+    SixStep,   // 1-D N = N1 * N2 beyond one plan: transpose, N1-point plan, twiddle + transpose, N2-point plan, transpose
     Generic,   // runtime mixed-radix (2,3,4,5,7,8,16) single CTA / multi-pass
     Bluestein, // chirp-z through a power-of-two convolution
     Ragged,    // persistent work-queue kernel over uneven lengths
@@ -73,7 +74,8 @@ struct fft_plan_s {
 
     b300fft::GraphPlan* gplan = nullptr;  // Generic / Ragged kinds
     fft_plan inner = nullptr;             // Real: the complex plan of N/2; TwoDTranspose: the rows plan
-    fft_plan inner2 = nullptr;            // TwoDTranspose: the plan over the transposed columns
+    fft_plan inner2 = nullptr;            // TwoDTranspose: the plan over the transposed columns; SixStep: N2
+    int64_t six_n1 = 0, six_n2 = 0;       // SixStep: N = six_n1 * six_n2 (inner: N1 points, inner2: N2 points)
     b300fft::TcPlan* tc = nullptr;
 
     int kernels = 0;
