@@ -34,6 +34,20 @@ def test_tc_parity(torch, mode, n, batch):
         assert err <= TOL[mode], (mode, n, d, err)
 
 
+@pytest.mark.parametrize("n,batch", [(4096, 4096), (65536, 256)])
+def test_precision_workload_against_oracle(torch, n, batch):
+    """The benchmark's precision workload (normal(0,1) seed 3, both shapes):
+    first, middle and last transforms of every mode against the FP64 oracle,
+    FP32 at 1e-6 and each tensor-core mode at its stated tolerance."""
+    x = inputs.normal_batch(batch, n, seed=3)
+    sample = [0, batch // 2, batch - 1]
+    ref = oracle.fft(x[sample], -1)
+    for mode, tol in [("fp32", 1e-6)] + list(TOL.items()):
+        y = run((n,), batch, x, -1, precision=mode)
+        err = max_rel_l2(y[sample], ref, -1)
+        assert err <= tol, (mode, n, err)
+
+
 @pytest.mark.parametrize("mode", ["tc_fp16", "tc_bf16"])
 def test_tc_dynamic_range(torch, mode):
     """Per-butterfly power-of-two scaling: a large constant offset (DC of
