@@ -148,8 +148,23 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             if (!want(0)) return FFT_OK;
             return exec_real(p, in, out, inv, st);
         case PlanKind::SixStep: {
-            // kernel sequence: transpose, the N1 plan's, twiddle-transpose, the N2 plan's, transpose
             const int64_t n1 = p->six_n1, n2 = p->six_n2, n = n1 * n2;
+            if (p->six_cols) {
+                // kernel sequence: columns (in -> workspace, with the twiddle), the N2 plan's
+                // (in place), transpose (workspace -> out); in == out is fine
+                const int kb = p->inner2->kernels;
+                fft_status s = FFT_OK;
+                if (want(0))
+                    e = launch_cols(8, 16, inv, true, in, p->d_work, n2, n2, n, p->batch, p->d_tables + p->off_a,
+                                    p->d_tables + p->off_lo, p->d_tables + p->off_hi, p->sh, st);
+                if (e == cudaSuccess && (only < 0 || (only >= 1 && only <= kb)))
+                    s = exec_plan(p->inner2, p->d_work, p->d_work, inv, st, only < 0 ? -1 : only - 1, per_size);
+                if (s == FFT_OK && e == cudaSuccess && want(kb + 1))
+                    e = launch_transpose(p->d_work, out, n1, n2, p->batch, st);
+                if (s != FFT_OK) return s;
+                break;
+            }
+            // kernel sequence: transpose, the N1 plan's, twiddle-transpose, the N2 plan's, transpose
             const int ka = p->inner->kernels, kb = p->inner2->kernels;
             const bool inplace = in == out;
             float2* t = inplace ? p->d_work : out;  // [N2][N1] between the first two steps

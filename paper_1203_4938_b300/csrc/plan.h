@@ -76,6 +76,7 @@ struct fft_plan_s {
     fft_plan inner = nullptr;             // Real: the complex plan of N/2; TwoDTranspose: the rows plan
     fft_plan inner2 = nullptr;            // TwoDTranspose: the plan over the transposed columns; SixStep: N2
     int64_t six_n1 = 0, six_n2 = 0;       // SixStep: N = six_n1 * six_n2 (inner: N1 points, inner2: N2 points)
+    bool six_cols = false;                // SixStep: N1 = 2^8 by the columns kernel (no inner, no first transpose)
     b300fft::TcPlan* tc = nullptr;
 
     int kernels = 0;

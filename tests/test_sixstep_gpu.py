@@ -25,11 +25,18 @@ def free(torch):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("form", ["columns", "transposing"])
 @pytest.mark.parametrize("n,batch", [(1 << 25, 2), (7 << 22, 1)])
-def test_sixstep_against_oracle(torch, n, batch):
+def test_sixstep_against_oracle(torch, monkeypatch, form, n, batch):
+    # columns: 256-point column transforms with the twiddle, N2 plan, one
+    # transpose; transposing: transpose, N1 plan, twiddle + transpose, N2
+    # plan, transpose (the form for lengths without a factor 2^8)
+    if form == "transposing":
+        monkeypatch.setenv("B300FFT_SIXSTEP_COLS", "0")
     x = inputs.normal_batch(batch, n, seed=n % 1000)
     with F.Plan((n,), batch) as p:
         assert p.describe().startswith("sixstep"), p.describe()
+        assert ("= 256 (columns, C=16, twiddle)" in p.describe()) == (form == "columns"), p.describe()
     for d in (-1, +1):
         y = run((n,), batch, x, d)
         assert max_rel_l2(y, oracle.fft(x, d), -1) <= TOL_FP32, (n, d)
@@ -86,7 +93,9 @@ def test_sixstep_2e30_impulse_and_round_trip(torch):
         free(torch)
 
 
-def test_sixstep_in_place_and_kernel_sequence(torch):
+@pytest.mark.parametrize("cols", ["1", "0"])
+def test_sixstep_in_place_and_kernel_sequence(torch, monkeypatch, cols):
+    monkeypatch.setenv("B300FFT_SIXSTEP_COLS", cols)
     n, batch = 1 << 25, 1
     x = to_dev(inputs.uniform_batch(batch, n, seed=4))
     with F.Plan((n,), batch) as p:
