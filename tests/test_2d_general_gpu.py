@@ -103,3 +103,25 @@ def test_real_plan_reports_inner_timeout(torch, monkeypatch):
         assert F.fft_plan_check(h) == F.FFT_OK
     finally:
         F.fft_plan_destroy(h)
+
+
+@pytest.mark.parametrize("shape,batch", [((96, 1009), 2), ((1 << 25,), 1), ((5 ** 11,), 1)])
+def test_per_size_form_matches(torch, shape, batch):
+    """fft_exec_per_size runs the inner stage-graph plans as one launch per
+    (stage, length) group; through the transposing 2-D plan and both six-step
+    forms it gives bitwise the values of fft_exec (the same tiles run, only
+    the launch split differs)."""
+    numel = batch
+    for s in shape:
+        numel *= s
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    x = torch.randn((batch,) + shape, dtype=torch.complex64, device="cuda", generator=g)
+    with F.Plan(shape, batch) as p:
+        a = p.forward(x).clone()
+        b = p.exec_per_size(x)
+        torch.cuda.synchronize()
+        p.check()
+        assert torch.equal(a, b), p.describe()
+    del x, a, b
+    torch.cuda.empty_cache()
