@@ -129,11 +129,13 @@ FFT_API fft_status fft_spectrum_product(const void *a, const void *b, void *out,
  * convolution among the DFT's uses):
  *     out[t] = scale * IDFT( DFT(x[t]) * H )          (conj_h = 0)
  *     out[t] = scale * IDFT( DFT(x[t]) * conj(H) )    (conj_h != 0)
- * with the unnormalised transforms of `plan` (a 1-D FP32 complex plan of n
- * points and batch rows; ragged and real plans: FFT_ERR_INVALID_ARG).
- * x, out: [batch][n] complex64; hspec: H = DFT(h), [n] complex64; device
- * pointers, 16-byte aligned; out == x allowed.  scale = 1/n gives the
- * circular convolution (correlation) of x with h.  Plans of a power of two
+ * with the unnormalised transforms of `plan` (an FP32 complex plan: 1-D of
+ * n points, or 2-D of n = H * W points, the circular 2-D filtering of every
+ * image; batch rows or images; ragged, real and tensor-core plans:
+ * FFT_ERR_INVALID_ARG).
+ * x, out: [batch][n] complex64; hspec: H = DFT(h), [n] complex64 (2-D:
+ * [H][W]); device pointers, 16-byte aligned; out == x allowed.  scale = 1/n
+ * gives the circular convolution (correlation) of x with h.  1-D plans of a power of two
  * n <= 2^14 run one fused pass per row (forward passes, product, inverse
  * passes in the tile: one HBM round trip); other plans run the forward
  * transform, fft_spectrum_product and the inverse transform through `out`.

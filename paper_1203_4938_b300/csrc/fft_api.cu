@@ -892,8 +892,7 @@ fft_status fft_convolve(fft_plan plan, const void* x, const void* hspec, void* o
                         void* stream) {
     if (!is_registered(plan)) return FFT_ERR_BAD_HANDLE;
     if (!x || !hspec || !out) return FFT_ERR_INVALID_ARG;
-    if (plan->dims != 1 || plan->precision != FFT_FP32 || plan->kind == PlanKind::Ragged ||
-        plan->kind == PlanKind::Real)
+    if (plan->precision != FFT_FP32 || plan->kind == PlanKind::Ragged || plan->kind == PlanKind::Real)
         return FFT_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(hspec) & 15) ||
         (reinterpret_cast<uintptr_t>(out) & 15))
@@ -907,8 +906,9 @@ fft_status fft_convolve(fft_plan plan, const void* x, const void* hspec, void* o
                                 scale, st) == cudaSuccess
                    ? FFT_OK
                    : FFT_ERR_CUDA;
+    const int64_t n = plan->len[0] * (plan->dims == 2 ? plan->len[1] : 1);  // points per transform
     fft_status s = exec_plan(plan, in, o, false, st);
-    if (s == FFT_OK) s = fft_spectrum_product(o, hs, o, plan->len[0], plan->batch, scale, conj_h, stream);
+    if (s == FFT_OK) s = fft_spectrum_product(o, hs, o, n, plan->batch, scale, conj_h, stream);
     if (s == FFT_OK) s = exec_plan(plan, o, o, true, st);
     return s;
 }

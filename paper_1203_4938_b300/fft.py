@@ -397,17 +397,13 @@ def convolve(x, h, corr: bool = False):
     with Plan(shape, batch) as px, Plan(shape, 1) as ph:
         H = ph.forward(h.reshape((1,) + shape).contiguous())
         s = torch.cuda.current_stream(x.device)
-        if len(shape) == 1:  # one call: fused for power-of-two lengths up to 2^14
-            out = torch.empty_like(x)
-            rc = fft_convolve(px.handle, x.data_ptr(), H.data_ptr(), out.data_ptr(), 1.0 / n, corr, s.cuda_stream)
-            if rc != FFT_OK:
-                raise FFTError(rc, "fft_convolve")
-            return out
-        X = px.forward(x)
-        rc = fft_spectrum_product(X.data_ptr(), H.data_ptr(), X.data_ptr(), n, batch, 1.0 / n, corr, s.cuda_stream)
+        # one call (fused for 1-D power-of-two lengths up to 2^14)
+        _check_tensor(x, px.numel, "input")
+        out = torch.empty_like(x)
+        rc = fft_convolve(px.handle, x.data_ptr(), H.data_ptr(), out.data_ptr(), 1.0 / n, corr, s.cuda_stream)
         if rc != FFT_OK:
-            raise FFTError(rc, "fft_spectrum_product")
-        return px.inverse(X)
+            raise FFTError(rc, "fft_convolve")
+        return out
 
 
 def image_steps(rgb, ux: float = 1.0, uy: float = 0.0, out=None):

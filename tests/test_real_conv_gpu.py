@@ -112,10 +112,13 @@ def test_convolution_1d(torch, n, batch, corr):
     assert max_rel_l2(y, ref, -1) <= 2 * TOL_FP32
 
 
-def test_convolution_2d_image_blur(torch):
-    """2-D circular filtering of image-shaped data (a 3x3 box kernel)."""
+@pytest.mark.parametrize("hgt,wid", [(64, 128), (60, 90), (96, 1009)])
+def test_convolution_2d_image_blur(torch, hgt, wid):
+    """2-D circular filtering of image-shaped data (a 3x3 box kernel) in one
+    fft_convolve call on a 2-D plan (in-place column kernels for 64 x 128,
+    the transposing plan for 60 x 90 and 96 x 1009), against the sum of
+    shifted images that defines it."""
     from paper_1203_4938_b300 import fft as F
-    hgt, wid = 64, 128
     img = inputs.image_batch(np.random.default_rng(1), 2, hgt, wid)
     k = np.zeros((hgt, wid), np.complex64)
     for dy in (-1, 0, 1):
