@@ -192,8 +192,23 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             break;
         }
         case PlanKind::TwoDTranspose: {
-            // kernel sequence: the rows plan's, transpose, the columns plan's, transpose
             const int64_t h = p->len[0], w = p->len[1];
+            if (!p->inner) {
+                // kernel sequence: transposed-store rows (in -> workspace [W][H]), the columns
+                // plan's (in place), transpose (workspace -> out); in == out is fine
+                const int kb = p->inner2->kernels;
+                fft_status s = FFT_OK;
+                if (want(0))
+                    e = launch_rowsT(p->logn_a, p->rowsT_tpc, inv, in, p->d_work, p->batch * h,
+                                     p->d_tables + p->off_a, h, st);
+                if (e == cudaSuccess && (only < 0 || (only >= 1 && only <= kb)))
+                    s = exec_plan(p->inner2, p->d_work, p->d_work, inv, st, only < 0 ? -1 : only - 1, per_size);
+                if (s == FFT_OK && e == cudaSuccess && want(kb + 1))
+                    e = launch_transpose(p->d_work, out, w, h, p->batch, st);
+                if (s != FFT_OK) return s;
+                break;
+            }
+            // kernel sequence: the rows plan's, transpose, the columns plan's, transpose
             const int ka = p->inner->kernels, kb = p->inner2->kernels;
             fft_status s = FFT_OK;
             if (only < 0 || only < ka) s = exec_plan(p->inner, in, out, inv, st, only < 0 ? -1 : only, per_size);

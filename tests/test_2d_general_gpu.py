@@ -47,13 +47,14 @@ def test_general_2d_in_place_round_trip(torch, h, w):
     assert max_rel_l2(z.reshape(1, -1), x.reshape(1, -1), -1) <= 2 * TOL_FP32
 
 
-def test_general_2d_kernel_sequence(torch):
-    # fft_exec_kernel k = 0 .. count-1 in order equals one fft_exec
-    h, w, batch = 96, 1009, 2
+@pytest.mark.parametrize("h,w,batch", [(96, 1009, 2), (8192, 512, 1)])
+def test_general_2d_kernel_sequence(torch, h, w, batch):
+    # fft_exec_kernel k = 0 .. count-1 in order equals one fft_exec (rows plan
+    # + two transposes, and the transposed-store rows form)
     x = to_dev(image(h, w, batch, 8))
     with F.Plan((h, w), batch) as p:
         n = F.fft_plan_kernel_count(p.handle)
-        assert n >= 4, n
+        assert n >= 3, n
         full = p.forward(x).clone()
         out = torch.empty_like(x)
         for k in range(n):
@@ -61,6 +62,23 @@ def test_general_2d_kernel_sequence(torch):
         torch.cuda.synchronize()
         p.check()
         assert torch.equal(out, full)
+
+
+@pytest.mark.parametrize("h,w,batch", [(8192, 512, 1), (1000, 64, 3), (36, 32, 5)])
+def test_general_2d_rows_form(torch, monkeypatch, h, w, batch):
+    """Power-of-two widths 2^5..2^12 with a height the in-place column
+    kernels do not take: the rows pass stores transposed (no first
+    transpose); the two-transpose form when that is switched off."""
+    x = image(h, w, batch, h + w)
+    ref = oracle.fft2(x, -1)
+    for rowst in ("1", "0"):
+        monkeypatch.setenv("B300FFT_2D_ROWST", rowst)
+        with F.Plan((h, w), batch) as p:
+            assert ("transposed store" in p.describe()) == (rowst == "1"), p.describe()
+        y = run((h, w), batch, x, -1)
+        assert max_rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1), -1) <= TOL_FP32, (h, w, rowst)
+        z = run((h, w), batch, x, +1, inplace=True)
+        assert max_rel_l2(z.reshape(batch, -1), oracle.fft2(x, +1).reshape(batch, -1), -1) <= TOL_FP32
 
 
 def test_general_2d_switched_off(torch, monkeypatch):
