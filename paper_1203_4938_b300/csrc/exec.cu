@@ -192,31 +192,32 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             break;
         }
         case PlanKind::TwoDTranspose: {
+            // kernel sequence: rows pass (transposed-store kernel, or the rows plan's kernels then a
+            // transpose) into the workspace [W][H]; columns pass (transposed-store kernel, or the
+            // columns plan's kernels in place then a transpose) into `out`.  in == out is fine.
             const int64_t h = p->len[0], w = p->len[1];
-            if (!p->inner) {
-                // kernel sequence: transposed-store rows (in -> workspace [W][H]), the columns
-                // plan's (in place), transpose (workspace -> out); in == out is fine
-                const int kb = p->inner2->kernels;
-                fft_status s = FFT_OK;
+            const int k1 = p->rowsT_tpc ? 1 : p->inner->kernels + 1;
+            const int k2 = p->cols_c ? 1 : p->inner2->kernels + 1;
+            fft_status s = FFT_OK;
+            if (p->rowsT_tpc) {
                 if (want(0))
                     e = launch_rowsT(p->logn_a, p->rowsT_tpc, inv, in, p->d_work, p->batch * h,
                                      p->d_tables + p->off_a, h, st);
-                if (e == cudaSuccess && (only < 0 || (only >= 1 && only <= kb)))
-                    s = exec_plan(p->inner2, p->d_work, p->d_work, inv, st, only < 0 ? -1 : only - 1, per_size);
-                if (s == FFT_OK && e == cudaSuccess && want(kb + 1))
-                    e = launch_transpose(p->d_work, out, w, h, p->batch, st);
-                if (s != FFT_OK) return s;
-                break;
+            } else {
+                if (only < 0 || only < k1 - 1) s = exec_plan(p->inner, in, out, inv, st, only, per_size);
+                if (s == FFT_OK && want(k1 - 1)) e = launch_transpose(out, p->d_work, h, w, p->batch, st);
             }
-            // kernel sequence: the rows plan's, transpose, the columns plan's, transpose
-            const int ka = p->inner->kernels, kb = p->inner2->kernels;
-            fft_status s = FFT_OK;
-            if (only < 0 || only < ka) s = exec_plan(p->inner, in, out, inv, st, only < 0 ? -1 : only, per_size);
-            if (s == FFT_OK && want(ka)) e = launch_transpose(out, p->d_work, h, w, p->batch, st);
-            if (s == FFT_OK && e == cudaSuccess && (only < 0 || (only > ka && only <= ka + kb)))
-                s = exec_plan(p->inner2, p->d_work, p->d_work, inv, st, only < 0 ? -1 : only - ka - 1, per_size);
-            if (s == FFT_OK && e == cudaSuccess && want(ka + kb + 1))
-                e = launch_transpose(p->d_work, out, w, h, p->batch, st);
+            if (s == FFT_OK && e == cudaSuccess) {
+                if (p->cols_c) {
+                    if (want(k1))
+                        e = launch_rowsT(p->logn_b, p->cols_c, inv, p->d_work, out, p->batch * w,
+                                         p->d_tables + p->off_b, w, st);
+                } else {
+                    if (only < 0 || (only >= k1 && only < k1 + k2 - 1))
+                        s = exec_plan(p->inner2, p->d_work, p->d_work, inv, st, only < 0 ? -1 : only - k1, per_size);
+                    if (s == FFT_OK && want(k1 + k2 - 1)) e = launch_transpose(p->d_work, out, w, h, p->batch, st);
+                }
+            }
             if (s != FFT_OK) return s;
             break;
         }

@@ -628,49 +628,65 @@ fft_status build_mixed_2d(fft_plan_s* p, int64_t h, int64_t w) {
 fft_status build_2d_transpose(fft_plan_s* p, int64_t h, int64_t w) {
     if (env_int("B300FFT_2D_TRANSPOSE", 1) == 0) return FFT_ERR_UNSUPPORTED;
     if (p->d_tables || p->d_work || p->d_aux || p->gplan) return FFT_ERR_UNSUPPORTED;  // a partly built plan
-    const int64_t lw = w, lh = h;
-    // W = 2^5..2^12: the rows pass is the four-step's transposed-row kernel,
-    // which writes [batch][W][H] straight away (tpc rows of one image per CTA,
-    // tpc*8-byte store runs), so the first transpose disappears.  Measured on
-    // a B300 (forward) against the rows plan + two transposes: 8192 x 4096
-    // 344 vs 386 us, 8192 x 512 x 8 303 vs 379 us, 16384 x 64 x 64 648 vs
-    // 835 us, 1000 x 1024 x 32 620 vs 705 us.
-    const int lw2 = ilog2_exact(w);
-    int tpc = 0;
-    if (env_int("B300FFT_2D_ROWST", 1) != 0 && lw2 >= 5 && lw2 <= 12)
-        for (int c = 16; c >= 4 && !tpc; c /= 2)
-            if (h % c == 0 && rowsT_threads(lw2, c) <= 1024 && rowsT_prepare(lw2, c) == cudaSuccess) tpc = c;
-    if (tpc) {
-        fft_status s = alloc_tables(p, (size_t)pow2_table_entries(lw2));
+    // A pass over rows of length L = 2^5..2^12 runs as the four-step's
+    // transposed-row kernel, which writes its output transposed straight away
+    // (tpc rows of one image per CTA, tpc*8-byte store runs), so the transpose
+    // after it disappears: the rows pass writes [batch][W][H] into the
+    // workspace, the columns pass writes [batch][H][W] into `out`.  Measured
+    // on a B300 (forward) against the plan + transpose form: rows pass
+    // 8192 x 4096 344 vs 386 us, 8192 x 512 x 8 303 vs 379 us, 16384 x 64 x 64
+    // 648 vs 835 us, 1000 x 1024 x 32 620 vs 705 us; columns pass 1024 x 1000
+    // x 32 621 vs 706 us, 4096 x 1000 x 8 658 vs 711 us.
+    const bool use = env_int("B300FFT_2D_ROWST", 1) != 0;
+    auto pick = [use](int64_t len, int64_t rows_per_image) {
+        const int l = ilog2_exact(len);
+        if (!use || l < 5 || l > 12) return 0;
+        for (int c = 16; c >= 4; c /= 2)
+            if (rows_per_image % c == 0 && rowsT_threads(l, c) <= 1024 && rowsT_prepare(l, c) == cudaSuccess) return c;
+        return 0;
+    };
+    const int tr = pick(w, h), tc = pick(h, w);  // rows pass: rows of W, H per image; columns: rows of H, W
+    const size_t ea = tr ? (size_t)pow2_table_entries(ilog2_exact(w)) : 0;
+    const size_t eb = tc ? (size_t)pow2_table_entries(ilog2_exact(h)) : 0;
+    if (ea + eb > 0) {
+        fft_status s = alloc_tables(p, ea + eb);
         if (s != FFT_OK) return s;
-        if (gen_pow2_table(p->d_tables, lw2, 0) != cudaSuccess) return FFT_ERR_CUDA;
         p->off_a = 0;
-        p->logn_a = lw2;
-        p->rowsT_tpc = tpc;
-    } else {
+        p->off_b = ea;
+        if (tr && gen_pow2_table(p->d_tables + p->off_a, ilog2_exact(w), 0) != cudaSuccess) return FFT_ERR_CUDA;
+        if (tc && gen_pow2_table(p->d_tables + p->off_b, ilog2_exact(h), 0) != cudaSuccess) return FFT_ERR_CUDA;
+    }
+    p->rowsT_tpc = tr;
+    p->cols_c = tc;  // TwoDTranspose: transposed-row width of the columns pass (0: plan + transpose)
+    p->logn_a = tr ? ilog2_exact(w) : 0;
+    p->logn_b = tc ? ilog2_exact(h) : 0;
+    const int64_t lw = w, lh = h;
+    if (!tr) {
         p->inner = fft_plan_create(1, &lw, p->batch * h, FFT_FP32);
         if (!p->inner) return fft_last_error();
     }
-    p->inner2 = fft_plan_create(1, &lh, p->batch * w, FFT_FP32);
-    if (!p->inner2) return fft_last_error();
+    if (!tc) {
+        p->inner2 = fft_plan_create(1, &lh, p->batch * w, FFT_FP32);
+        if (!p->inner2) return fft_last_error();
+    }
     p->work_bytes = (size_t)h * (size_t)w * (size_t)p->batch * sizeof(float2);
     if (cudaMalloc(&p->d_work, p->work_bytes) != cudaSuccess) return FFT_ERR_ALLOC;
     p->kind = PlanKind::TwoDTranspose;
-    if (tpc) {
-        p->kernels = 1 + fft_plan_kernel_count(p->inner2) + 1;
-        char b2[140];
-        fft_plan_describe(p->inner2, b2, sizeof b2);
-        std::snprintf(p->desc, sizeof p->desc,
-                      "2d-transpose H=%lld W=%lld: rows with transposed store (tpc=%d), columns [%s], transpose",
-                      (long long)h, (long long)w, tpc, b2);
-        return FFT_OK;
+    p->kernels = (tr ? 1 : fft_plan_kernel_count(p->inner) + 1) + (tc ? 1 : fft_plan_kernel_count(p->inner2) + 1);
+    char a[110] = "", b[110] = "";
+    if (tr) std::snprintf(a, sizeof a, "rows with transposed store (tpc=%d)", tr);
+    else {
+        std::snprintf(a, sizeof a, "rows [");
+        fft_plan_describe(p->inner, a + 6, sizeof a - 8);
+        std::strncat(a, "], transpose", sizeof a - std::strlen(a) - 1);
     }
-    p->kernels = fft_plan_kernel_count(p->inner) + 1 + fft_plan_kernel_count(p->inner2) + 1;
-    char a[110], b[110];
-    fft_plan_describe(p->inner, a, sizeof a);
-    fft_plan_describe(p->inner2, b, sizeof b);
-    std::snprintf(p->desc, sizeof p->desc, "2d-transpose H=%lld W=%lld: rows [%s], transpose, columns [%s], transpose",
-                  (long long)h, (long long)w, a, b);
+    if (tc) std::snprintf(b, sizeof b, "columns with transposed store (tpc=%d)", tc);
+    else {
+        std::snprintf(b, sizeof b, "columns [");
+        fft_plan_describe(p->inner2, b + 9, sizeof b - 11);
+        std::strncat(b, "], transpose", sizeof b - std::strlen(b) - 1);
+    }
+    std::snprintf(p->desc, sizeof p->desc, "2d-transpose H=%lld W=%lld: %s, %s", (long long)h, (long long)w, a, b);
     return FFT_OK;
 }
 

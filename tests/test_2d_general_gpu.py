@@ -47,7 +47,7 @@ def test_general_2d_in_place_round_trip(torch, h, w):
     assert max_rel_l2(z.reshape(1, -1), x.reshape(1, -1), -1) <= 2 * TOL_FP32
 
 
-@pytest.mark.parametrize("h,w,batch", [(96, 1009, 2), (8192, 512, 1)])
+@pytest.mark.parametrize("h,w,batch", [(96, 1009, 2), (8192, 512, 1), (1024, 1000, 1), (1000, 1024, 1)])
 def test_general_2d_kernel_sequence(torch, h, w, batch):
     # fft_exec_kernel k = 0 .. count-1 in order equals one fft_exec (rows plan
     # + two transposes, and the transposed-store rows form)
@@ -64,11 +64,17 @@ def test_general_2d_kernel_sequence(torch, h, w, batch):
         assert torch.equal(out, full)
 
 
-@pytest.mark.parametrize("h,w,batch", [(8192, 512, 1), (1000, 64, 3), (36, 32, 5)])
-def test_general_2d_rows_form(torch, monkeypatch, h, w, batch):
-    """Power-of-two widths 2^5..2^12 with a height the in-place column
-    kernels do not take: the rows pass stores transposed (no first
-    transpose); the two-transpose form when that is switched off."""
+@pytest.mark.parametrize("h,w,batch,force", [(8192, 512, 1, False), (1000, 64, 3, False), (36, 32, 5, False),
+                                             (1024, 1000, 1, False), (64, 36, 3, False), (64, 128, 2, True),
+                                             (4096, 32, 1, True)])
+def test_general_2d_transposed_store_forms(torch, monkeypatch, h, w, batch, force):
+    """A pass over rows of 2^5..2^12 points stores transposed (the
+    four-step's transposed-row kernel, no transpose after it): the rows pass
+    for such widths, the columns pass for such heights, both when the plan is
+    forced on two power-of-two sides; the plan + transpose form when that is
+    switched off."""
+    if force:
+        monkeypatch.setenv("B300FFT_2D_TRANSPOSE", "2")
     x = image(h, w, batch, h + w)
     ref = oracle.fft2(x, -1)
     for rowst in ("1", "0"):
