@@ -197,7 +197,7 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             // columns plan's kernels in place then a transpose) into `out`.  in == out is fine.
             const int64_t h = p->len[0], w = p->len[1];
             const int k1 = p->rowsT_tpc ? 1 : p->inner->kernels + 1;
-            const int k2 = p->cols_c ? 1 : p->inner2->kernels + 1;
+            const int k2 = p->colsT_tpc ? 1 : p->inner2->kernels + 1;
             fft_status s = FFT_OK;
             if (p->rowsT_tpc) {
                 if (want(0))
@@ -208,9 +208,9 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
                 if (s == FFT_OK && want(k1 - 1)) e = launch_transpose(out, p->d_work, h, w, p->batch, st);
             }
             if (s == FFT_OK && e == cudaSuccess) {
-                if (p->cols_c) {
+                if (p->colsT_tpc) {
                     if (want(k1))
-                        e = launch_rowsT(p->logn_b, p->cols_c, inv, p->d_work, out, p->batch * w,
+                        e = launch_rowsT(p->logn_b, p->colsT_tpc, inv, p->d_work, out, p->batch * w,
                                          p->d_tables + p->off_b, w, st);
                 } else {
                     if (only < 0 || (only >= k1 && only < k1 + k2 - 1))

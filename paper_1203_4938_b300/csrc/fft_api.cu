@@ -657,7 +657,7 @@ fft_status build_2d_transpose(fft_plan_s* p, int64_t h, int64_t w) {
         if (tc && gen_pow2_table(p->d_tables + p->off_b, ilog2_exact(h), 0) != cudaSuccess) return FFT_ERR_CUDA;
     }
     p->rowsT_tpc = tr;
-    p->cols_c = tc;  // TwoDTranspose: transposed-row width of the columns pass (0: plan + transpose)
+    p->colsT_tpc = tc;
     p->logn_a = tr ? ilog2_exact(w) : 0;
     p->logn_b = tc ? ilog2_exact(h) : 0;
     const int64_t lw = w, lh = h;

@@ -51,7 +51,8 @@ struct fft_plan_s {
     int mix_mh = 0, mix_mw = 0;  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
     bool real_fused = false;     // Real: one-pass fused rows + split kernel (h = 2^5 .. 2^12)
     int cols_c = 0;     // columns kernel width
-    int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA
+    int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA (TwoDTranspose: of the rows pass, 0: plan + transpose)
+    int colsT_tpc = 0;  // TwoDTranspose: transposed-rows kernel rows per CTA of the columns pass (0: plan + transpose)
 
     // persistent four-step
     int pl1 = 0, pc = 0, pl2 = 0, ptpc = 0;
