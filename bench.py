@@ -456,6 +456,12 @@ def run_gpu(args):
                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
                "overlap": "copies on two side streams, double-buffered, overlapping the transforms"}
 
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = run_config_keys(args, peak, OracleLeg(not args.no_cpu))
+    if world > 1:
+        dist.barrier()
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         gf, secs, threads, desc = oracle_sample(1 << 19 if args.quick else 1 << 21)
@@ -490,6 +496,8 @@ def run_gpu(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if configs:
+            line["configs"] = configs
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -511,6 +519,215 @@ def _time_stream(fn, steps, warmup):
     a1.record()
     torch.cuda.synchronize()
     return a0.elapsed_time(a1) / steps
+
+
+def _rel_rows(y, ref):
+    """Per-row relative L2 distance of y from ref (FP64), along the last axis."""
+    y = np.asarray(y, np.complex128)
+    ref = np.asarray(ref, np.complex128)
+    return np.sqrt(np.sum(np.abs(y - ref) ** 2, -1)) / np.sqrt(np.sum(np.abs(ref) ** 2, -1))
+
+
+def _is_prime(n: int) -> bool:
+    if n < 2:
+        return False
+    i = 2
+    while i * i <= n:
+        if n % i == 0:
+            return False
+        i += 1
+    return True
+
+
+class OracleLeg:
+    """The CPU-baseline leg's oracle runs beside the other workloads: each
+    config's sample is transformed by the FP64 oracle on the host cores (its
+    time is that config's CPU baseline) and the GPU result of the same
+    transforms is compared with it (relative L2, max over the sample).
+    Disabled with --no-cpu, in which case no oracle code runs."""
+
+    def __init__(self, enabled: bool):
+        self.enabled = enabled
+        self.oracle = None
+        if enabled:
+            import oracle
+            oracle.build()
+            self.oracle = oracle
+
+    def run(self, fn):
+        """(result, seconds) of fn(oracle), or (None, None) when disabled."""
+        if not self.enabled:
+            return None, None
+        t0 = time.perf_counter()
+        r = fn(self.oracle)
+        return r, time.perf_counter() - t0
+
+
+def _ragged_errors(orc, lengths, offsets, data, y, sign):
+    """Max per-transform relative L2 error of the ragged result y: the full
+    oracle FFT for composite lengths, the definition for primes up to 4096
+    points, 24 bins of the definition for longer primes."""
+    groups = {}
+    for t, n in enumerate(lengths):
+        groups.setdefault(int(n), []).append(t)
+    worst, sampled = 0.0, 0
+    for n, ts in groups.items():
+        xs = np.stack([data[offsets[t]:offsets[t + 1]] for t in ts])
+        ys = np.stack([y[offsets[t]:offsets[t + 1]] for t in ts])
+        if _is_prime(n) and n > 4096:
+            ks = np.unique(np.concatenate([[0, 1, n - 1, n // 2], np.random.default_rng(n).integers(0, n, 20)]))
+            for j in range(len(ts)):
+                vals = orc.dft_bins(xs[j], ks, sign)
+                worst = max(worst, float(np.linalg.norm(ys[j][ks] - vals) / np.linalg.norm(vals)))
+                sampled += 1
+            continue
+        ref = orc.dft_naive(xs, sign) if _is_prime(n) else orc.fft(xs, sign)
+        worst = max(worst, float(_rel_rows(ys, ref).max()))
+    return worst, sampled
+
+
+def run_config_keys(args, peak: float, leg: OracleLeg) -> dict:
+    """The other four workloads, each timed on the GPU (CUDA events on the
+    current stream, inputs resident in HBM) and, through the CPU-baseline leg,
+    compared with the FP64 oracle:
+      small      N=1024 x 64, uniform[-1,1] seed 0, forward (1000 execs per
+                 CUDA graph replay: launch-latency bound), every transform;
+      image2d    1 x 4096^2 and 16 x 2048^2 image-shaped, seed 2, forward then
+                 inverse; oracle on the 4096^2 image and two 2048^2 images,
+                 round trip on all;
+      precision  4096 x 4096 and 256 x 65536, normal(0,1) seed 3, forward, in
+                 every mode (FP32 and the four tensor-core modes); oracle on
+                 the first, middle and last transforms;
+      ragged     10,000 uneven lengths, seed 4, forward and inverse, one
+                 persistent graph launch vs launches per (stage, length);
+                 oracle on every transform."""
+    import torch
+    from paper_1203_4938_b300 import fft as F
+    steps, warm = max(3, min(args.steps, 10)), 3
+    out = {}
+
+    def hbm(bytes_, ms):
+        gbs = bytes_ / (ms * 1e-3) / 1e9
+        return {"algorithmic_gbs": gbs, "roofline_frac": gbs / peak}
+
+    # --- small
+    n, bt, reps = 1024, 64, 1000
+    xh = inputs.uniform_batch(bt, n, seed=0)
+    x = torch.from_numpy(xh).cuda()
+    y = torch.empty_like(x)
+    with F.Plan((n,), bt) as p:
+        p.forward(x, y)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            p.forward(x, y)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(reps):
+                    p.forward(x, y)
+        ms = _time_stream(g.replay, 3, 2) / reps
+        p.forward(x, y)
+        torch.cuda.synchronize()
+        p.check()
+        yh = y.cpu().numpy()
+        plan = p.describe()
+    ref, secs = leg.run(lambda o: o.fft(xh, -1))
+    out["small"] = {"workload": "N=1024 x 64 forward, uniform[-1,1] seed 0", "us_per_exec": ms * 1e3,
+                    "gflops": 5.0 * n * math.log2(n) * bt / (ms * 1e-3) / 1e9, **hbm(16.0 * n * bt, ms),
+                    "note": "launch-latency bound (graph replay of 1000 execs); 1 MiB per exec stays in L2",
+                    "rel_l2_vs_oracle_max": None if ref is None else float(_rel_rows(yh, ref).max()),
+                    "oracle_sample": "all 64 transforms", "oracle_seconds": secs, "plan": plan}
+    del x, y
+
+    # --- image2d
+    a, b = inputs.image_workload(seed=2)
+    parts = {}
+    for name, arr, samp in (("4096x4096", a, [0]), ("16x2048x2048", b, [0, 15])):
+        bt, h, w = arr.shape
+        x = torch.from_numpy(arr).cuda()
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        with F.Plan((h, w), bt) as p:
+            def step():
+                p.forward(x, y)
+                p.inverse(y, z)
+            ms = _time_stream(step, steps, warm)
+            step()
+            torch.cuda.synchronize()
+            p.check()
+            plan = p.describe()
+        ys = y[samp].cpu().numpy().reshape(len(samp), -1)
+        rt = (z.reshape(bt, -1) / (h * w) - x.reshape(bt, -1)).norm(dim=-1) / x.reshape(bt, -1).norm(dim=-1)
+        ref, secs = leg.run(lambda o: o.fft2(arr[samp], -1).reshape(len(samp), -1))
+        part = {"ms_fwd_inv": ms, "gflops": 2 * bt * 5.0 * h * w * math.log2(h * w) / (ms * 1e-3) / 1e9,
+                **hbm(2 * 16.0 * bt * h * w, ms), "round_trip_rel_l2_max": float(rt.max().item()), "plan": plan,
+                "oracle_sample": f"forward of image(s) {samp}", "oracle_seconds": secs}
+        if ref is not None:
+            part["rel_l2_vs_oracle_max"] = float(_rel_rows(ys, ref).max())
+            ref_nodc, ys_nodc = ref.copy(), ys.copy()
+            ref_nodc[:, 0] = 0
+            ys_nodc[:, 0] = 0
+            part["rel_l2_vs_oracle_max_without_dc"] = float(_rel_rows(ys_nodc, ref_nodc).max())
+        parts[name] = part
+        del x, y, z
+    tot_ms = sum(v["ms_fwd_inv"] for v in parts.values())
+    tot_gf = sum(v["gflops"] * v["ms_fwd_inv"] for v in parts.values()) / tot_ms
+    out["image2d"] = {"workload": "1x4096^2 + 16x2048^2 image-shaped, seed 2, forward + inverse",
+                      "ms_fwd_inv": tot_ms, "gflops": tot_gf, "parts": parts}
+
+    # --- precision
+    parts = {}
+    for n, bt in ((4096, 4096), (65536, 256)):
+        xh = inputs.normal_batch(bt, n, seed=3)
+        samp = [0, bt // 2, bt - 1]
+        x = torch.from_numpy(xh).cuda()
+        y = torch.empty_like(x)
+        ref, secs = leg.run(lambda o: o.fft(xh[samp], -1))
+        for mode in ("fp32", "tc_fp16", "tc_bf16", "tc_fp16_plain", "tc_bf16_plain"):
+            with F.Plan((n,), bt, mode) as p:
+                ms = _time_stream(lambda: p.forward(x, y), steps, warm)
+                p.forward(x, y)
+                torch.cuda.synchronize()
+                p.check()
+                yh = y[samp].cpu().numpy()
+                parts[f"{bt}x{n} {mode}"] = {
+                    "us": ms * 1e3, "gflops": bt * 5.0 * n * math.log2(n) / (ms * 1e-3) / 1e9,
+                    **hbm(16.0 * bt * n, ms), "plan": p.describe(),
+                    "rel_l2_vs_oracle_max": None if ref is None else float(_rel_rows(yh, ref).max())}
+        parts[f"{bt}x{n} oracle"] = {"oracle_sample": "transforms 0, B/2, B-1", "oracle_seconds": secs}
+        del x, y
+    out["precision"] = {"workload": "4096x4096 and 256x65536, normal(0,1) seed 3, forward", "parts": parts}
+
+    # --- ragged
+    lengths, offsets, data = inputs.ragged_workload(10000, seed=4)
+    lens = [int(v) for v in lengths]
+    x = torch.from_numpy(data).cuda()
+    y = torch.empty_like(x)
+    fl = sum(5.0 * n * math.log2(n) for n in lens if n > 1)
+    with F.Ragged(lens) as p:
+        ms_p = _time_stream(lambda: p.exec(x, y), steps, warm)
+        ms_s = _time_stream(lambda: p.exec_per_size(x, y), steps, warm)
+        errs, secs_tot = {}, 0.0
+        for sign in (-1, +1):
+            p.exec(x, y, sign)
+            torch.cuda.synchronize()
+            p.check()
+            if leg.enabled:
+                yh = y.cpu().numpy()
+                r, secs = leg.run(lambda o: _ragged_errors(o, lens, offsets, data, yh, sign))
+                errs["forward" if sign < 0 else "inverse"] = r[0]
+                secs_tot += secs
+        plan = p.describe()
+    out["ragged"] = {"workload": "10,000 lengths (2^6..2^16, 3/5/7*2^k, ~1% primes), seed 4, forward",
+                     "elements": int(offsets[-1]), "ms_persistent_graph": ms_p, "ms_per_size_launches": ms_s,
+                     "gflops": fl / (ms_p * 1e-3) / 1e9, "gflops_per_size_launches": fl / (ms_s * 1e-3) / 1e9,
+                     "persistent_over_per_size": ms_s / ms_p, **hbm(16.0 * offsets[-1], ms_p), "plan": plan,
+                     "rel_l2_vs_oracle_max": errs or None,
+                     "oracle_sample": "all 10,000 transforms (24 bins for primes above 4096)",
+                     "oracle_seconds": secs_tot if leg.enabled else None}
+    del x, y
+    torch.cuda.synchronize()
+    return out
 
 
 def run_ragged(args):
@@ -824,6 +1041,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="1/16 of the batch (smoke runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="sweep only (no small/image2d/precision/ragged keys)")
     ap.add_argument("--no-tune", action="store_true", help="ragged: planner defaults instead of measured tiles")
     args = ap.parse_args()
     if args.impl == "reference":

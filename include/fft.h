@@ -217,8 +217,12 @@ FFT_API fft_status fft_exec_kernel(fft_plan plan, int k, const void *in, void *o
  * at start-up) -- and so cannot create a plan, whose tables and workspace are
  * allocated.  It computes the same transform as a plan for (1, {n}, batch)
  * with the same two-pass kernels, but keeps its workspace and twiddle tables
- * in arrays that are part of the library image: every GPU that loads the
- * library holds them (about 32.1 MiB) until the process exits.
+ * in arrays that are part of the library image: every GPU on which the
+ * library's device code is loaded holds them (about 32.1 MiB) until the
+ * process exits.  Under CUDA's default lazy module loading that memory is
+ * committed at the first call on each device, not when the library is
+ * loaded: make one call per device before the host fixes its device-memory
+ * budget (and before any stream capture).
  *   in, out    device pointers, 16-byte aligned, batch * n complex64 each
  *              ([batch][n]); in == out is allowed.
  *   n          a power of two, 2^13 <= n <= 2^22.
@@ -227,12 +231,12 @@ FFT_API fft_status fft_exec_kernel(fft_plan plan, int k, const void *in, void *o
  *   direction  FFT_FORWARD or FFT_INVERSE;  stream  a cudaStream_t or NULL.
  * Allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
  * The first call on a device looks up the device addresses of the static
- * arrays and sets kernel attributes for that device; make that first call
- * before any stream capture.  Every call on a device shares the same arrays
- * (the tables are rebuilt on the stream by each call, the workspace is fully
- * overwritten before it is read), so calls whose execution overlaps on the
- * GPU -- on different streams, or from different threads -- race and give
- * wrong results; order them on one stream.  Asynchronous like fft_exec. */
+ * arrays and sets kernel attributes for that device.  Every call on a device
+ * shares the same arrays: the twiddle tables are rebuilt on the stream only
+ * when n differs from the previous call's on that device, and the workspace
+ * is fully overwritten before it is read, so calls whose execution overlaps
+ * on the GPU -- on different streams, or from different threads -- race and
+ * give wrong results; order them on one stream.  Asynchronous like fft_exec. */
 FFT_API fft_status fft_exec_pow2_static(const void *in, void *out, int64_t n, int64_t batch, int direction,
                                         void *stream);
 

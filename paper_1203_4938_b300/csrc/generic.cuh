@@ -97,6 +97,7 @@ struct GExecArgs {
     int64_t spin_limit;
     int single;  // per-stage launch: item = item0 + blockIdx.x, no waits
     int item0;
+    int withhold_xf;  // fault injection for tests: transform whose first stage never signals (-1: none)
     const int64_t* line_off;  // element offsets of grouped lines (GStage::line_tab)
 };
 
@@ -625,7 +626,7 @@ __device__ __forceinline__ void g_run_item(const GExecArgs& a, int p, float2* sm
     }
     if (s + 1 < x.nstages && !a.single) {
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !(s == 0 && t == a.withhold_xf)) {
             __threadfence();
             atomicAdd(a.ctl + 1 + x.ctr + s, 1);
         }

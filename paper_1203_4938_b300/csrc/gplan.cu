@@ -507,6 +507,7 @@ GExecArgs make_args(const GraphPlan* gp, const float2* in, float2* out, bool inv
     a.single = single;
     a.item0 = item0;
     a.line_off = gp->line_off;
+    a.withhold_xf = gp->withhold_xf;
     return a;
 }
 
@@ -741,18 +742,29 @@ fft_status build_impl(GraphPlan* gp, const std::vector<int64_t>& lengths, int64_
         woff += (k.w2 + 1) & ~int64_t(1);
         xf.push_back(x);
     };
+    // test-only fault injection: the caller's transform number `wh` (its
+    // record, when it has one of its own) never signals its first stage
+    const int64_t wh = env_i("B300FFT_DEBUG_WITHHOLD_XF", -1);
+    gp->withhold_xf = -1;
     if (ragged) {
         for (auto& kv : kinds)
             if (kv.second.group) add_xf(kv.first, 0);  // one transform holds every line of the length
-        for (int64_t n : lengths) {
-            if (!kinds[n].group) add_xf(n, off);
+        for (size_t i = 0; i < lengths.size(); ++i) {
+            const int64_t n = lengths[i];
+            if (!kinds[n].group) {
+                if ((int64_t)i == wh) gp->withhold_xf = (int)xf.size();
+                add_xf(n, off);
+            }
             off += n;
         }
     } else {
         const int64_t n = lengths[0];
         if (kinds[n].lines > 1) add_xf(n, 0);
         else
-            for (int64_t b = 0; b < batch; ++b) add_xf(n, b * n);
+            for (int64_t b = 0; b < batch; ++b) {
+                if (b == wh) gp->withhold_xf = (int)xf.size();
+                add_xf(n, b * n);
+            }
     }
     if ((int64_t)xf.size() >= (int64_t(1) << 31)) return FFT_ERR_UNSUPPORTED;
 

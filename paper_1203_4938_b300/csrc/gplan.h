@@ -56,6 +56,7 @@ struct GraphPlan {
     int kfull = 0, klean = 0;
     int nrest = 0, grid_lean = 0;
     int64_t spin_limit = int64_t(1) << 23;
+    int withhold_xf = -1;  // test-only fault injection (B300FFT_DEBUG_WITHHOLD_XF)
     std::string desc;
     int64_t* line_off = nullptr;              // grouped-line offsets (device)
     bool no_tune = false;                     // candidate plans built by the autotuner

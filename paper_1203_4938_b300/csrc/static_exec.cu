@@ -6,8 +6,12 @@
 // -- inside a memory-pool-less real-time loop, a plugin whose host forbids
 // allocation after start-up, or a caller that budgets every device byte up
 // front -- can still run a large 1-D transform.  The arrays below are part
-// of the library image, so every GPU that loads the library holds them
-// (about 32.1 MiB) until the process exits.
+// of the library image: every GPU on which the library's device code is
+// loaded holds them (about 32.1 MiB) until the process exits.  Under CUDA's
+// default lazy module loading this file's module is loaded, and the 32.1 MiB
+// committed, at the first call on each device (the cudaGetSymbolAddress of
+// the set-up), so a caller should make one call per device before it fixes
+// its device-memory budget, and before any stream capture.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,6 +35,7 @@ std::mutex g_static_mu;
 bool g_static_ready[kMaxDevices] = {};
 float2* g_static_work_ptr[kMaxDevices] = {};
 float2* g_static_tab_ptr[kMaxDevices] = {};
+int64_t g_static_tab_n[kMaxDevices] = {};  // n whose tables the device's array holds (0: none)
 
 // Once per device, with that device current: device addresses of the static
 // arrays (the host-side symbols are not device addresses) and the
@@ -91,17 +96,26 @@ extern "C" fft_status fft_exec_pow2_static(const void* in, void* out, int64_t n,
     while (tpc > 2 && (rowsT_threads(l2, tpc) > 1024 || n1 % tpc != 0)) tpc /= 2;
     if (c == 0 || rowsT_threads(l2, tpc) > 1024 || n1 % tpc != 0) return FFT_ERR_UNSUPPORTED;
 
-    // twiddle tables of this n, rebuilt on the caller's stream every call
+    // twiddle tables of this n, built on the caller's stream when the
+    // device's array holds another length's (calls are ordered on the GPU, so
+    // a later call with the same n reads what an earlier one wrote)
     float2* tab = g_static_tab_ptr[dev];
     const int sh = (logn + 1) / 2;
     const int64_t ea = pow2_table_entries(l1), eb = pow2_table_entries(l2);
     const int64_t elo = int64_t(1) << sh, ehi = int64_t(1) << (logn - sh);
     const int64_t off_b = ea, off_lo = ea + eb, off_hi = off_lo + elo;
     if (off_hi + ehi > kStaticTableEntries) return FFT_ERR_UNSUPPORTED;
-    if (gen_pow2_table(tab, l1, st) != cudaSuccess) return FFT_ERR_CUDA;
-    if (gen_pow2_table(tab + off_b, l2, st) != cudaSuccess) return FFT_ERR_CUDA;
-    if (gen_root_table(tab + off_lo, elo, 1, n, st) != cudaSuccess) return FFT_ERR_CUDA;
-    if (gen_root_table(tab + off_hi, ehi, elo, n, st) != cudaSuccess) return FFT_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (g_static_tab_n[dev] != n) {
+            g_static_tab_n[dev] = 0;
+            if (gen_pow2_table(tab, l1, st) != cudaSuccess) return FFT_ERR_CUDA;
+            if (gen_pow2_table(tab + off_b, l2, st) != cudaSuccess) return FFT_ERR_CUDA;
+            if (gen_root_table(tab + off_lo, elo, 1, n, st) != cudaSuccess) return FFT_ERR_CUDA;
+            if (gen_root_table(tab + off_hi, ehi, elo, n, st) != cudaSuccess) return FFT_ERR_CUDA;
+            g_static_tab_n[dev] = n;
+        }
+    }
 
     float2* work = g_static_work_ptr[dev];
     const float2* x = static_cast<const float2*>(in);
