@@ -61,7 +61,10 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             a.withhold_chunk = p->withhold_chunk;
             e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch), st);
             if (e == cudaSuccess)
-                e = launch_fourstep_persist(PersistConfig{p->pl1, p->pc, p->pl2, p->ptpc}, inv, a, p->pgrid, st);
+                e = p->ppipe ? launch_fourstep_pipe(PersistConfig{p->pl1, p->pc, p->pl2, p->ptpc}, p->ppipe, inv, a,
+                                                    p->pgrid, st)
+                             : launch_fourstep_persist(PersistConfig{p->pl1, p->pc, p->pl2, p->ptpc}, inv, a, p->pgrid,
+                                                       st);
             break;
         }
         case PlanKind::ThreeStep: {
@@ -91,7 +94,8 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             a.withhold_chunk = p->withhold_chunk;
             e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch + (int64_t)p->pnch * p->pG), st);
             if (e == cudaSuccess)
-                e = launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2}, inv, a, p->pgrid, st);
+                e = p->ppipe ? launch_threestep_pipe(ThreeConfig{p->pl1, p->pc, p->pl2}, p->ppipe, inv, a, p->pgrid, st)
+                             : launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2}, inv, a, p->pgrid, st);
             break;
         }
         case PlanKind::TwoDPersist: {

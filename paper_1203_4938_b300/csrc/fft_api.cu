@@ -108,21 +108,38 @@ fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
         {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
         {7, 32, 8, 16, 32}, {8, 16, 8, 16, 16}, {8, 16, 9, 8, 32}, {8, 16, 10, 4, 32}, {9, 16, 10, 8, 16},
         {10, 8, 10, 8, 16}, {11, 4, 10, 8, 16}, {11, 4, 11, 4, 32}, {12, 4, 11, 8, 48}, {12, 4, 12, 4, 8}};
-    const bool forced = std::getenv("B300FFT_PERSIST_CFG") != nullptr;
+    const Pow2Choice* force = pow2_forced();
+    if (force && force->family != 2) force = nullptr;
+    const bool forced = force || std::getenv("B300FFT_PERSIST_CFG") != nullptr;
     if (logn > 24 || (kCfg[logn][0] == 0 && !forced)) return FFT_ERR_UNSUPPORTED;
     PersistConfig cfg{kCfg[logn][0], kCfg[logn][1], kCfg[logn][2], kCfg[logn][3]};
     if (const char* v = std::getenv("B300FFT_PERSIST_CFG")) {
         PersistConfig o{};
         if (std::sscanf(v, "%d,%d,%d,%d", &o.l1, &o.c, &o.l2, &o.tpc) == 4 && o.l1 + o.l2 == logn) cfg = o;
     }
-    if (!persist_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+    if (force) cfg = PersistConfig{force->a, force->b, force->c, force->d};
+    if (cfg.l1 + cfg.l2 != logn) return FFT_ERR_UNSUPPORTED;
+    // Asynchronous-load form (k_pipe.cu): slots in its shared-memory ring per
+    // log2 N, 0 = the plain persistent kernel (measured slower at every size
+    // of the sweep, so off by default; B300FFT_PIPE=2 or 3 selects it).
+    const int pipe_ns = force ? force->pipe : env_int("B300FFT_PIPE", 0);
     PersistInfo info;
-    if (persist_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    p->ppipe = 0;
+    if (pipe_ns && pipe_config_available(cfg, pipe_ns) && pipe_prepare(cfg, pipe_ns, &info) == cudaSuccess &&
+        info.blocks_per_sm >= 1) {
+        p->ppipe = pipe_ns;
+    } else {
+        if (!persist_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+        if (persist_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t n = int64_t(1) << logn, n1 = int64_t(1) << cfg.l1, n2 = int64_t(1) << cfg.l2;
-    const int64_t chunk_bytes = int64_t(env_int("B300FFT_CHUNK_MB", kCfg[logn][4] ? kCfg[logn][4] : 32)) << 20;
+    const int64_t chunk_bytes =
+        int64_t(force && force->chunk_mb ? force->chunk_mb
+                                         : env_int("B300FFT_CHUNK_MB", kCfg[logn][4] ? kCfg[logn][4] : 32))
+        << 20;
     int64_t cb = chunk_bytes / (n * 8);
     if (cb < 1) cb = 1;
     if (cb > p->batch) cb = p->batch;
@@ -162,8 +179,9 @@ fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
     if (cudaMalloc(&p->d_aux, sizeof(int) * (size_t)(1 + nch)) != cudaSuccess) return FFT_ERR_ALLOC;
     p->kernels = 1;
     std::snprintf(p->desc, sizeof p->desc,
-                  "fourstep-persist N=2^%d = 2^%d (C=%d) x 2^%d (tpc=%d) threads=%d grid=%d chunk=%lld x %lld",
-                  logn, cfg.l1, cfg.c, cfg.l2, cfg.tpc, info.threads, p->pgrid, (long long)cb, (long long)nch);
+                  "fourstep-persist N=2^%d = 2^%d (C=%d) x 2^%d (tpc=%d) threads=%d grid=%d chunk=%lld x %lld%s",
+                  logn, cfg.l1, cfg.c, cfg.l2, cfg.tpc, info.threads, p->pgrid, (long long)cb, (long long)nch,
+                  p->ppipe == 3 ? " tma-ring=3" : (p->ppipe == 2 ? " tma-ring=2" : ""));
     return FFT_OK;
 }
 
@@ -181,16 +199,29 @@ static const int kThree[25][5] = {
 bool three_preferred(int logn) { return logn >= 0 && logn <= 24 && kThree[logn][4] != 0; }
 
 fft_status build_threestep(fft_plan_s* p, int logn) {
+    const Pow2Choice* force = pow2_forced();
+    if (force && force->family != 3) force = nullptr;
     const char* forced = std::getenv("B300FFT_THREE_CFG");
-    if (logn > 24 || (kThree[logn][0] == 0 && !forced)) return FFT_ERR_UNSUPPORTED;
+    if (logn > 24 || (kThree[logn][0] == 0 && !forced && !force)) return FFT_ERR_UNSUPPORTED;
     ThreeConfig cfg{kThree[logn][0], kThree[logn][1], kThree[logn][2]};
     if (forced) {
         ThreeConfig o{};
         if (std::sscanf(forced, "%d,%d,%d", &o.la, &o.lb1, &o.lb2) == 3 && o.la + o.lb1 + o.lb2 == logn) cfg = o;
     }
-    if (cfg.la + cfg.lb1 + cfg.lb2 != logn || !three_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+    if (force) cfg = ThreeConfig{force->a, force->b, force->c};
+    if (cfg.la + cfg.lb1 + cfg.lb2 != logn) return FFT_ERR_UNSUPPORTED;
+    // asynchronous-load form (k_three_pipe.cu): ring slots, 0 = plain kernel
+    // (measured slower at every size, so off by default)
+    const int pipe_ns = force ? force->pipe : env_int("B300FFT_PIPE", 0);
     PersistInfo info;
-    if (three_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    p->ppipe = 0;
+    if (pipe_ns && three_pipe_available(cfg, pipe_ns) && three_pipe_prepare(cfg, pipe_ns, &info) == cudaSuccess &&
+        info.blocks_per_sm >= 1) {
+        p->ppipe = pipe_ns;
+    } else {
+        if (!three_config_available(cfg)) return FFT_ERR_UNSUPPORTED;
+        if (three_prepare(cfg, &info) != cudaSuccess || info.blocks_per_sm < 1) return FFT_ERR_CUDA;
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -199,7 +230,9 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     const int64_t n2 = m1 * m2;
     const int64_t ca = 4096 >> cfg.la, cb_cols = 4096 >> cfg.lb1, tpc = 4096 >> cfg.lb2;
     const int64_t chunk_bytes =
-        int64_t(env_int("B300FFT_CHUNK_MB", kThree[logn][3] ? kThree[logn][3] : 32)) << 20;
+        int64_t(force && force->chunk_mb ? force->chunk_mb
+                                         : env_int("B300FFT_CHUNK_MB", kThree[logn][3] ? kThree[logn][3] : 32))
+        << 20;
     int64_t cb = chunk_bytes / (n * 8);
     if (cb < 1) cb = 1;
     if (cb > p->batch) cb = p->batch;
@@ -224,7 +257,7 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     p->pgrid = (int)(items < slots ? items : slots);
     // B1 lookahead: at least twice the CTAs in flight between a B1 tile and its first consumer
     int64_t D = (2 * (int64_t)p->pgrid + nb1g - 1) / nb1g;
-    D = env_int("B300FFT_THREE_LOOKAHEAD", (int)D);
+    D = force && force->lookahead > 0 ? force->lookahead : env_int("B300FFT_THREE_LOOKAHEAD", (int)D);
     if (D < 1) D = 1;
     if (D > G) D = G;
     p->pD = (int)D;
@@ -252,9 +285,9 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     if (cudaMalloc(&p->d_aux, sizeof(int) * (size_t)(1 + nch + nch * G)) != cudaSuccess) return FFT_ERR_ALLOC;
     p->kernels = 1;
     std::snprintf(p->desc, sizeof p->desc,
-                  "threestep N=2^%d = 2^%d x (2^%d x 2^%d) threads=%d grid=%d chunk=%lld x %lld groups=%lld ahead=%lld",
+                  "threestep N=2^%d = 2^%d x (2^%d x 2^%d) threads=%d grid=%d chunk=%lld x %lld groups=%lld ahead=%lld%s",
                   logn, cfg.la, cfg.lb1, cfg.lb2, info.threads, p->pgrid, (long long)cb, (long long)nch, (long long)G,
-                  (long long)D);
+                  (long long)D, p->ppipe == 3 ? " tma-ring=3" : (p->ppipe == 2 ? " tma-ring=2" : ""));
     return FFT_OK;
 }
 
@@ -306,8 +339,29 @@ fft_status build_cluster(fft_plan_s* p, int logn, bool forced) {
 }
 
 fft_status build_pow2_1d(fft_plan_s* p, int logn) {
+    // FFT_AUTOTUNE=1: time the candidate kernels and shapes for this length and
+    // batch (tune_pow2.cu) and build the fastest
+    Pow2Choice pick;
+    if (!pow2_forced() && env_int("FFT_AUTOTUNE", 0) != 0 && tune_pow2(logn, p->batch, &pick)) {
+        pow2_force(&pick);
+        fft_status s = build_pow2_1d(p, logn);
+        pow2_force(nullptr);
+        return s;
+    }
+    const Pow2Choice* force = pow2_forced();
+    if (force) {  // exactly the forced family, or unsupported
+        if (force->family == 1) {
+            if (logn > kRowsMaxLog) return FFT_ERR_UNSUPPORTED;
+        } else if (force->family == 2) {
+            return build_fourstep_persist(p, logn);
+        } else if (force->family == 3) {
+            return build_threestep(p, logn);
+        } else {
+            return FFT_ERR_UNSUPPORTED;
+        }
+    }
     p->single_max_log = env_int("B300FFT_SINGLE_MAX_LOG", p->single_max_log);
-    if (logn <= p->single_max_log && logn <= kRowsMaxLog) {
+    if (force || (logn <= p->single_max_log && logn <= kRowsMaxLog)) {
         p->kind = PlanKind::Rows;
         p->logn_a = logn;
         p->off_a = 0;

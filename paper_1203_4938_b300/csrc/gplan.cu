@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -554,10 +555,13 @@ void tune_cache_load() {
     if (!path) return;
     FILE* f = std::fopen(path, "r");
     if (!f) return;
-    char key[256];
-    GLenConfig c;
-    while (std::fscanf(f, "%255s %d %d %d %d", key, &c.tile_max, &c.split_n2, &c.lpt_a, &c.lpt_b) == 5)
-        g_tune_cache[key] = c;
+    char line[512], key[256];
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::strncmp(line, "pow2:", 5) == 0) continue;  // the batched power-of-two tuner's lines
+        GLenConfig c;
+        if (std::sscanf(line, "%255s %d %d %d %d", key, &c.tile_max, &c.split_n2, &c.lpt_a, &c.lpt_b) == 5)
+            g_tune_cache[key] = c;
+    }
     std::fclose(f);
 }
 

@@ -1,6 +1,7 @@
 // launch.h -- host-side entry points of the kernel translation units, used by
 // the plan/ABI layer (fft_api.cu).  Internal to the library.
 #pragma once
+#include <cuda.h>  // CUtensorMap (descriptor type only; the driver API is not linked)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -106,6 +107,24 @@ cudaError_t persist_prepare(const PersistConfig& c, PersistInfo* info);
 cudaError_t launch_fourstep_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid,
                                     cudaStream_t st);
 
+// --- tensor maps of the asynchronous tile copies (k_pipe.cu) -----------------
+// Encode a tiled tensor map over 8-byte elements (complex64): dims[0] is the
+// innermost extent, strides_bytes[i] the byte stride of dimension i + 1, box
+// the copied box (each extent <= 256).  False when the driver's encoder is
+// unavailable or refuses the layout.
+bool tensor_maps_available();
+bool encode_tensor_map(CUtensorMap* tm, const void* base, int rank, const uint64_t* dims,
+                       const uint64_t* strides_bytes, const uint32_t* box);
+
+// --- persistent four-step with asynchronous tile loads (k_pipe.cu) ----------
+// The same decomposition as launch_fourstep_persist, run by a producer warp
+// (tensor-memory-accelerator copies into a ring of ns = 2 or 3 shared-memory
+// slots) and the consumer warps of one tile per CTA.
+bool pipe_config_available(const PersistConfig& c, int ns);
+cudaError_t pipe_prepare(const PersistConfig& c, int ns, PersistInfo* info);
+cudaError_t launch_fourstep_pipe(const PersistConfig& c, int ns, bool inv, const PersistArgs& a, int grid,
+                                 cudaStream_t st);
+
 // --- persistent 2-D (k_2d.cu) --------------------------------------------------
 // PersistConfig fields: l1 = log2 W, c = rows per row tile, l2 = log2 H,
 // tpc = columns per column tile.
@@ -122,6 +141,11 @@ struct ThreeConfig {
 bool three_config_available(const ThreeConfig& c);
 cudaError_t three_prepare(const ThreeConfig& c, PersistInfo* info);
 cudaError_t launch_threestep(const ThreeConfig& c, bool inv, const ThreeArgs& a, int grid, cudaStream_t st);
+// The same with asynchronous tile loads (pipe3.cuh) into a ring of ns = 2 or 3 slots.
+bool three_pipe_available(const ThreeConfig& c, int ns);
+cudaError_t three_pipe_prepare(const ThreeConfig& c, int ns, PersistInfo* info);
+cudaError_t launch_threestep_pipe(const ThreeConfig& c, int ns, bool inv, const ThreeArgs& a, int grid,
+                                  cudaStream_t st);
 
 // --- thread-block-cluster single pass (k_cluster.cu) --------------------------
 // N = K * 2^lm (K = 8 or 16 CTAs per transform, DSMEM exchanges).

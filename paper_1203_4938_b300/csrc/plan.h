@@ -56,6 +56,7 @@ struct fft_plan_s {
 
     // persistent four-step
     int pl1 = 0, pc = 0, pl2 = 0, ptpc = 0;
+    int ppipe = 0;  // > 0: the persistent four-step runs with asynchronous loads into a ring of ppipe slots
     int pgrid = 0, pnch = 0, pna = 0, pnb = 0;
     int64_t pcb = 0;
     int64_t spin_limit = int64_t(1) << 23;
@@ -85,6 +86,25 @@ struct fft_plan_s {
 };
 
 namespace b300fft {
+
+// An explicit choice for the batched power-of-two planner: what the
+// autotuner times as a candidate and returns as its pick.
+struct Pow2Choice {
+    int family = 0;     // 1 single-pass rows, 2 persistent four-step, 3 persistent three-stage
+    int a = 0, b = 0, c = 0, d = 0;  // four-step: l1, columns, l2, rows per tile; three-stage: la, lb1, lb2
+    int chunk_mb = 0;   // transforms per dependency chunk, in MiB (0: table)
+    int pipe = 0;       // ring slots of the asynchronous-load form (0: plain loads)
+    int lookahead = 0;  // three-stage B1 lookahead in row groups (0: planner's rule)
+};
+// The calling thread's forced choice (null: tables and environment decide).
+const Pow2Choice* pow2_forced();
+void pow2_force(const Pow2Choice* c);
+// Time the candidates for transforms of 2^logn x batch on the current device
+// and return the fastest in *best (false when there is nothing to choose).
+// Results are cached per process and, when FFT_TUNE_CACHE names a file, in
+// that file (lines "pow2:<device>:<logn>:<batch> family a b c d chunk pipe
+// lookahead us").
+bool tune_pow2(int logn, int64_t batch, Pow2Choice* best);
 
 void destroy_plan_resources(fft_plan_s* p);
 // only < 0: every kernel; else only kernel `only` of the sequence

@@ -94,6 +94,14 @@ __device__ __forceinline__ uint64_t l2_policy_evict_last() {
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+// Shared-memory store that the compiler keeps after the memory operations
+// before it: thread 0 of a persistent CTA publishes the next queue item
+// (an atomic's result) only after issuing its own loads of the current tile,
+// so waiting for the atomic never delays those loads.
+__device__ __forceinline__ void st_shared_after(int* p, int v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
 // Drop a 128-byte L2 line without writing it back (scratch data only).
 __device__ __forceinline__ void l2_discard_line(const void* p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
@@ -104,25 +112,75 @@ __device__ __forceinline__ void dft_at(float2* v) {
     dft<R, 0, S, INV>(v);
 }
 
+// Twiddles of a radix-16 pass P >= 1 that read six table entries per
+// butterfly (W^k, W^2k, W^3k, W^4k, W^8k, W^12k; the other nine are one
+// complex product of two of them).  They can be loaded ahead of the pass --
+// before the exchange barrier that precedes it, where the data registers are
+// free -- so the table loads' latency overlaps the barrier instead of
+// stalling the butterflies.
+template <class PL, int P>
+struct TwPre {
+    static constexpr bool ON = P > 0 && P < PL::NPASS && PL::radix(P) == 16 && kTwiddleLoads6;
+    static constexpr int Q = ON ? PL::R / 16 : 1;
+    float2 w[Q][6];
+};
+
+__device__ __forceinline__ float2 ldg_nc_f2(const float2* p) {
+    float2 r;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+    return r;
+}
+
+// Issue the table loads of pass P for butterflies b0 + q*T (no-op unless
+// TwPre<PL, P>::ON).  The loads are volatile so the compiler keeps them ahead
+// of the barrier that follows.
+template <class PL, int P>
+__device__ __forceinline__ void tw_preload(TwPre<PL, P>& pre, int b0, const float2* __restrict__ tw) {
+    if constexpr (TwPre<PL, P>::ON) {
+        constexpr int Ns = PL::ns(P);
+#pragma unroll
+        for (int q = 0; q < TwPre<PL, P>::Q; ++q) {
+            const float2* tp = tw + PL::twoff(P) + ((b0 + q * PL::T) & (Ns - 1));
+            pre.w[q][0] = ldg_nc_f2(tp);
+            pre.w[q][1] = ldg_nc_f2(tp + Ns);
+            pre.w[q][2] = ldg_nc_f2(tp + 2 * Ns);
+            pre.w[q][3] = ldg_nc_f2(tp + 3 * Ns);
+            pre.w[q][4] = ldg_nc_f2(tp + 7 * Ns);
+            pre.w[q][5] = ldg_nc_f2(tp + 11 * Ns);
+        }
+    }
+}
+
 // Multiply the butterfly inputs of pass P by their twiddles and run the
 // radix-R_P butterflies.  b0 = t (butterfly index of q = 0); butterfly q is
-// b0 + q*T and owns v[q + Q*r].
+// b0 + q*T and owns v[q + Q*r].  `pre`: the pass's table entries loaded
+// ahead by tw_preload (null: loaded here).
 template <class PL, int P, bool INV>
-__device__ __forceinline__ void pass_compute(float2 (&v)[PL::R], int b0, const float2* __restrict__ tw) {
+__device__ __forceinline__ void pass_compute(float2 (&v)[PL::R], int b0, const float2* __restrict__ tw,
+                                             const TwPre<PL, P>* pre = nullptr) {
     constexpr int Rp = PL::radix(P), Q = PL::R / Rp, Ns = PL::ns(P);
     if constexpr (P > 0 && Rp == 16 && kTwiddleLoads6) {
         // six table loads (W^k, W^2k, W^3k, W^4k, W^8k, W^12k); the other nine
         // twiddles are one complex product of two table values each
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const float2* tp = tw + PL::twoff(P) + ((b0 + q * PL::T) & (Ns - 1));
             float2 w[16];
-            w[1] = __ldg(tp);
-            w[2] = __ldg(tp + Ns);
-            w[3] = __ldg(tp + 2 * Ns);
-            w[4] = __ldg(tp + 3 * Ns);
-            w[8] = __ldg(tp + 7 * Ns);
-            w[12] = __ldg(tp + 11 * Ns);
+            if (pre) {
+                w[1] = pre->w[q][0];
+                w[2] = pre->w[q][1];
+                w[3] = pre->w[q][2];
+                w[4] = pre->w[q][3];
+                w[8] = pre->w[q][4];
+                w[12] = pre->w[q][5];
+            } else {
+                const float2* tp = tw + PL::twoff(P) + ((b0 + q * PL::T) & (Ns - 1));
+                w[1] = __ldg(tp);
+                w[2] = __ldg(tp + Ns);
+                w[3] = __ldg(tp + 2 * Ns);
+                w[4] = __ldg(tp + 3 * Ns);
+                w[8] = __ldg(tp + 7 * Ns);
+                w[12] = __ldg(tp + 11 * Ns);
+            }
 #pragma unroll
             for (int h = 4; h <= 12; h += 4)
 #pragma unroll
@@ -189,11 +247,36 @@ __device__ __forceinline__ void pass_gather(float2 (&v)[PL::R], int t, const flo
     }
 }
 
+// Barrier over the threads of a tile: the whole CTA (NB = 0), or the first
+// NB threads on named barrier 1 (tiles run by the consumer warps of a
+// warp-specialised kernel, whose producer warp does not take part).
+template <int NB>
+__device__ __forceinline__ void tile_sync() {
+    if constexpr (NB == 0) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+}
+
+// Barrier over the first NB threads (named barrier 1) that also returns
+// whether `v` holds in every one of them.
+template <int NB>
+__device__ __forceinline__ bool tile_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.and.pred po, 1, %2, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NB)
+        : "memory");
+    return r != 0;
+}
+
 // Barrier over the threads that share an exchange buffer.
-template <bool WARP_ONLY>
+template <bool WARP_ONLY, int NB = 0>
 __device__ __forceinline__ void xsync() {
     if constexpr (WARP_ONLY) __syncwarp();
-    else __syncthreads();
+    else tile_sync<NB>();
 }
 
 // All passes from P on (CS interleaved columns in the exchange buffer).  With
@@ -201,32 +284,44 @@ __device__ __forceinline__ void xsync() {
 // then rewrites the exchange area only after a barrier of its own (tile loop,
 // CTA exit, cluster barrier).  Measured: faster for the column tiles of the
 // persistent kernels, slower for the single-pass rows kernel.
-template <class PL, int P, bool INV, bool WARP_ONLY, int CS, bool LAST_SYNC = true>
+template <class PL, int P, bool INV, bool WARP_ONLY, int CS, bool LAST_SYNC = true, int NB = 0>
 __device__ __forceinline__ void run_passes(float2 (&v)[PL::R], int t, float2* s, int coff,
-                                           const float2* __restrict__ tw) {
-    pass_compute<PL, P, INV>(v, t, tw);
+                                           const float2* __restrict__ tw, const TwPre<PL, P>* pre = nullptr) {
+    pass_compute<PL, P, INV>(v, t, tw, pre);
     if constexpr (P + 1 < PL::NPASS) {
         pass_scatter<PL, P, CS>(v, t, s, coff);
-        xsync<WARP_ONLY>();
+        TwPre<PL, P + 1> next;
+        tw_preload<PL, P + 1>(next, t, tw);  // in flight across the barrier
+        xsync<WARP_ONLY, NB>();
         pass_gather<PL, CS>(v, t, s, coff);
-        if constexpr (LAST_SYNC || P + 2 < PL::NPASS) xsync<WARP_ONLY>();
-        run_passes<PL, P + 1, INV, WARP_ONLY, CS, LAST_SYNC>(v, t, s, coff, tw);
+        if constexpr (LAST_SYNC || P + 2 < PL::NPASS) xsync<WARP_ONLY, NB>();
+        run_passes<PL, P + 1, INV, WARP_ONLY, CS, LAST_SYNC, NB>(v, t, s, coff, tw,
+                                                                  TwPre<PL, P + 1>::ON ? &next : nullptr);
     }
 }
 
 // Passes P .. NPASS-2, ending with the scatter of the inputs of the last pass
 // into the exchange buffer and a barrier (the caller gathers them with its own
 // thread mapping).  Requires NPASS >= 2.
-template <class PL, int P, bool INV>
+// The twiddles of each following pass are loaded ahead of the barrier before
+// it; those of the last pass for its re-mapped butterfly index t_last, into
+// `last`.
+template <class PL, int P, bool INV, int NB = 0>
 __device__ __forceinline__ void run_passes_to_last(float2 (&v)[PL::R], int t, float2* s,
-                                                   const float2* __restrict__ tw) {
-    pass_compute<PL, P, INV>(v, t, tw);
+                                                   const float2* __restrict__ tw, const TwPre<PL, P>* pre,
+                                                   TwPre<PL, PL::NPASS - 1>& last, int t_last) {
+    pass_compute<PL, P, INV>(v, t, tw, pre);
     pass_scatter<PL, P, 1>(v, t, s, 0);
-    __syncthreads();
     if constexpr (P + 2 < PL::NPASS) {
+        TwPre<PL, P + 1> next;
+        tw_preload<PL, P + 1>(next, t, tw);
+        tile_sync<NB>();
         pass_gather<PL, 1>(v, t, s, 0);
-        __syncthreads();
-        run_passes_to_last<PL, P + 1, INV>(v, t, s, tw);
+        tile_sync<NB>();
+        run_passes_to_last<PL, P + 1, INV, NB>(v, t, s, tw, TwPre<PL, P + 1>::ON ? &next : nullptr, last, t_last);
+    } else {
+        tw_preload<PL, PL::NPASS - 1>(last, t_last, tw);
+        tile_sync<NB>();
     }
 }
 
@@ -282,7 +377,7 @@ struct RowsTCfg {
 
 // Everything after the load: v holds x[t + i*T] of row `sub` (thread
 // (sub, t), t = threadIdx.x mod T).
-template <int LOGN, int TPC, bool INV, St SK>
+template <int LOGN, int TPC, bool INV, St SK, int NB = 0>
 __device__ __forceinline__ void rowsT_tile_regs(float2 (&v)[P2Plan<LOGN>::R], float2* __restrict__ dst, int64_t n1,
                                                 const float2* __restrict__ tw, float2* smem, uint64_t pol) {
     using CF = RowsTCfg<LOGN, TPC>;
@@ -290,9 +385,10 @@ __device__ __forceinline__ void rowsT_tile_regs(float2 (&v)[P2Plan<LOGN>::R], fl
     static_assert(PL::NPASS >= 2, "transposed rows need at least two passes");
     const int t = threadIdx.x & (PL::T - 1);
     const int sub = threadIdx.x / PL::T;
-    run_passes_to_last<PL, 0, INV>(v, t, smem + sub * CF::PITCH, tw);
     const int c = threadIdx.x % TPC;
     const int t2 = threadIdx.x / TPC;
+    TwPre<PL, PL::NPASS - 1> last;
+    run_passes_to_last<PL, 0, INV, NB>(v, t, smem + sub * CF::PITCH, tw, nullptr, last, t2);
     const float2* sc = smem + c * CF::PITCH;
     if constexpr (PL::T % 16 == 0) {
         const float2* p = sc + padi(t2);
@@ -302,7 +398,7 @@ __device__ __forceinline__ void rowsT_tile_regs(float2 (&v)[P2Plan<LOGN>::R], fl
 #pragma unroll
         for (int i = 0; i < PL::R; ++i) v[i] = sc[padi(t2 + i * PL::T)];
     }
-    pass_compute<PL, PL::NPASS - 1, INV>(v, t2, tw);
+    pass_compute<PL, PL::NPASS - 1, INV>(v, t2, tw, TwPre<PL, PL::NPASS - 1>::ON ? &last : nullptr);
     float2* d0 = dst + c;
 #pragma unroll
     for (int i = 0; i < PL::R; ++i) stx<SK>(d0 + n1 * (int64_t)(t2 + i * PL::T), v[i], pol);
@@ -346,25 +442,29 @@ __device__ __forceinline__ float2 root2(const float2* __restrict__ lo, const flo
 // Everything after the load: v holds x[t + i*T] of column c (thread (c, t)).
 // With TW the twiddle of element (k1, n2) is W^{tws*n2*k1} of the two-level
 // table (tws > 1 reuses a longer transform's table for a divisor length).
-template <int LOGN, int C, bool INV, bool TW, St SK>
+// `steps_buf` (C * 16 float2) holds the per-column twiddle steps; null: right
+// after the exchange buffer (smem + XBUF).
+template <int LOGN, int C, bool INV, bool TW, St SK, int NB = 0>
 __device__ __forceinline__ void cols_tile_regs(float2 (&v)[P2Plan<LOGN>::R], float2* __restrict__ dst, int64_t S,
                                                uint32_t col0, const float2* __restrict__ tw,
                                                const float2* __restrict__ tw_lo, const float2* __restrict__ tw_hi,
-                                               int sh, float2* smem, uint64_t pol, uint32_t tws = 1) {
+                                               int sh, float2* smem, uint64_t pol, uint32_t tws = 1,
+                                               float2* steps_buf = nullptr) {
     using CF = ColsCfg<LOGN, C>;
     using PL = typename CF::PL;
     const int c = threadIdx.x % C;
     const int t = threadIdx.x / C;
-    float2* steps = smem + CF::XBUF;  // [R][C]: W^{n2*T*i} (column fastest: conflict-free reads)
+    // [R][C]: W^{n2*T*i} (column fastest: conflict-free reads)
+    float2* steps = steps_buf ? steps_buf : smem + CF::XBUF;
     if constexpr (TW) {
         for (int j = threadIdx.x; j < C * PL::R; j += CF::THREADS) {
             const int cc = j % C, ii = j / C;
             steps[ii * C + cc] = root2(tw_lo, tw_hi, (col0 + (uint32_t)cc) * tws * (uint32_t)(ii * PL::T), sh);
         }
-        if constexpr (PL::NPASS == 1) __syncthreads();
+        if constexpr (PL::NPASS == 1) tile_sync<NB>();
     }
 
-    run_passes<PL, 0, INV, false, C, false>(v, t, smem, c, tw);
+    run_passes<PL, 0, INV, false, C, false, NB>(v, t, smem, c, tw);
 
     if constexpr (TW) {
         const float2 w0 = root2(tw_lo, tw_hi, (col0 + (uint32_t)c) * tws * (uint32_t)t, sh);

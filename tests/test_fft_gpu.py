@@ -169,6 +169,19 @@ def test_side_stream_and_graph_capture(torch):
     (13, {"B300FFT_SINGLE_MAX_LOG": "12"}),                       # two-launch four-step
     (14, {"B300FFT_SINGLE_MAX_LOG": "12"}),
     (16, {"B300FFT_PERSIST": "0"}),                              # two-launch instead of persistent
+    (16, {"B300FFT_PIPE": "0"}),                                 # persistent kernel with plain loads
+    # persistent four-step fed by tensor-memory-accelerator copies (ring of 2 or 3 slots)
+    (15, {"B300FFT_PIPE": "2"}),
+    (15, {"B300FFT_PIPE": "3", "B300FFT_PERSIST_CFG": "8,16,7,32"}),
+    (16, {"B300FFT_PIPE": "3", "B300FFT_CHUNK_MB": "1"}),        # many chunks, ragged last chunk
+    (16, {"B300FFT_PIPE": "2", "B300FFT_CHUNK_MB": "64"}),       # one chunk: B tiles wait on A tiles
+    (17, {"B300FFT_PIPE": "2"}),
+    (18, {"B300FFT_PIPE": "3", "B300FFT_PERSIST_CFG": "9,8,9,8"}),
+    (19, {"B300FFT_PIPE": "3", "B300FFT_PERSIST_CFG": "9,8,10,4"}),
+    (19, {"B300FFT_PIPE": "2"}),
+    (20, {"B300FFT_PIPE": "3", "B300FFT_PERSIST_CFG": "10,4,10,4"}),
+    (20, {"B300FFT_PIPE": "2", "B300FFT_PERSIST_CFG": "10,4,10,4", "B300FFT_CHUNK_MB": "4"}),
+    (20, {"B300FFT_PIPE": "0"}),
     (20, {"B300FFT_PERSIST": "0"}),
     (17, {"B300FFT_CHUNK_MB": "1"}),                             # many chunks, ragged last chunk
     (18, {"B300FFT_PERSIST_CFG": "9,8,9,8", "B300FFT_CHUNK_MB": "3"}),
@@ -204,7 +217,7 @@ def test_fourstep_variants(torch, monkeypatch, logn, env):
         assert max_rel_l2(y, oracle.fft(x, d), -1) <= TOL_FP32, (logn, env, d)
 
 
-@pytest.mark.parametrize("cfg", [None, "8,8,8,8", "three"])
+@pytest.mark.parametrize("cfg", [None, "8,8,8,8", "three", "pipe2"])
 def test_persistent_wait_timeout_is_reported(torch, monkeypatch, cfg):
     """A chunk counter that nothing ever completes makes the bounded waits of
     the second-pass tiles expire: the kernel returns, the plan reports
@@ -218,6 +231,8 @@ def test_persistent_wait_timeout_is_reported(torch, monkeypatch, cfg):
         x = to_dev(inputs.uniform_batch(b, n, seed=9))
         monkeypatch.setenv("B300FFT_THREE", "1")
         monkeypatch.setenv("B300FFT_THREE_CFG", "6,6,7")
+    elif cfg == "pipe2":
+        monkeypatch.setenv("B300FFT_PIPE", "2")
     elif cfg:
         monkeypatch.setenv("B300FFT_PERSIST_CFG", cfg)
     monkeypatch.setenv("B300FFT_DEBUG_WITHHOLD_CHUNK", "0")
