@@ -35,33 +35,15 @@ LO, HI = 10, 24
 METRIC = "C2C FFT GFLOP/s (5N*log2N/t), fwd+inv sweep N=2^10..2^24, 2^26 complex64 per size"
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, MB per launch)
-# of each sweep size's kernel at the full sweep size (2^26 elements), from the
-# single-pass ncu launch list of `python bench.py --steps 1 --warmup 1 --no-e2e
-# --no-cpu` (mean of the forward and inverse launches).  The numbers belong to
-# the kernel sources hashed in TRAFFIC_SOURCES and to the plans described in
-# MEASURED_PLANS (split, tile shape, chunking); when either differs the
-# benchmark reports the traffic as null until a new capture replaces them.
-MEASURED_DRAM_MB = {10: 1018, 11: 1020, 12: 1020, 13: 1022, 14: 1021, 15: 1356, 16: 1017, 17: 1420, 18: 1457, 19: 1023, 20: 1125, 21: 1396, 22: 1356, 23: 2017, 24: 2167}
-MEASURED_PLANS = {
-    10: "rows N=2^10 tpc=4 threads=256",
-    11: "rows N=2^11 tpc=2 threads=256",
-    12: "rows N=2^12 tpc=1 threads=256",
-    13: "rows N=2^13 tpc=1 threads=256",
-    14: "rows N=2^14 tpc=1 threads=512",
-    15: "fourstep-persist N=2^15 = 2^7 (C=32) x 2^8 (tpc=16) threads=256 grid=592 chunk=128 x 16",
-    16: "fourstep-persist N=2^16 = 2^8 (C=16) x 2^8 (tpc=16) threads=256 grid=592 chunk=32 x 32",
-    17: "fourstep-persist N=2^17 = 2^8 (C=16) x 2^9 (tpc=8) threads=256 grid=592 chunk=32 x 16",
-    18: "fourstep-persist N=2^18 = 2^8 (C=16) x 2^10 (tpc=4) threads=256 grid=592 chunk=16 x 16",
-    19: "fourstep-persist N=2^19 = 2^9 (C=16) x 2^10 (tpc=8) threads=512 grid=296 chunk=4 x 32",
-    20: "fourstep-persist N=2^20 = 2^10 (C=8) x 2^10 (tpc=8) threads=512 grid=296 chunk=2 x 32",
-    21: "threestep N=2^21 = 2^7 x (2^7 x 2^7) threads=256 grid=592 chunk=2 x 16 groups=8 ahead=8",
-    22: "threestep N=2^22 = 2^7 x (2^7 x 2^8) threads=256 grid=592 chunk=1 x 16 groups=8 ahead=8",
-    23: "threestep N=2^23 = 2^8 x (2^7 x 2^8) threads=256 grid=592 chunk=1 x 8 groups=16 ahead=10",
-    24: "threestep N=2^24 = 2^8 x (2^8 x 2^8) threads=256 grid=592 chunk=1 x 4 groups=16 ahead=5"}
-TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threestep.cuh", "kernels_launch.cuh",
-                   "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu"]
-TRAFFIC_SOURCES_SHA = "5320d4467e90d0f2"
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum per launch) of
+# each sweep size's kernel at the full sweep size (2^26 elements), from the
+# one-kernel ncu captures summarised in profiles/sweep_dram_traffic.md.  The
+# numbers belong to the kernel sources hashed there and to the plan printed
+# beside each size; when either differs the benchmark reports the traffic as
+# null until a new capture replaces them.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_dram_traffic.md")
+TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threestep.cuh", "tma.cuh",
+                   "kernels_launch.cuh", "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu"]
 
 
 def traffic_sources_sha() -> str:
@@ -74,19 +56,36 @@ def traffic_sources_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def traffic_table(path: str = TRAFFIC_FILE):
+    """(sources hash, {log2 N: (plan, DRAM bytes per launch)}) parsed from the
+    profile summary; ({}, None) when it is missing."""
+    sha, rows = None, {}
+    try:
+        with open(path) as fh:
+            for line in fh:
+                if line.startswith("Kernel sources hash:"):
+                    sha = line.split(":", 1)[1].strip().strip("`")
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) >= 3 and cells[0].isdigit():
+                    rows[int(cells[0])] = (cells[1].strip("`"), float(cells[2]) * 1e6)
+    except OSError:
+        return None, {}
+    return sha, rows
+
+
 def measured_traffic(logn: int, plan_desc: str):
     """DRAM bytes per launch of the sweep kernel for 2^logn, or None when the
     kernel sources or the plan differ from the captured ones (or the size was
     not captured)."""
+    sha, rows = traffic_table()
     try:
-        if traffic_sources_sha() != TRAFFIC_SOURCES_SHA:
+        if sha is None or traffic_sources_sha() != sha:
             return None
     except OSError:
         return None
-    if MEASURED_PLANS.get(logn) != plan_desc:
+    if logn not in rows or rows[logn][0] != plan_desc:
         return None
-    mb = MEASURED_DRAM_MB.get(logn)
-    return None if mb is None else mb * 1e6
+    return rows[logn][1]
 
 
 def flops_per_step(lo=LO, hi=HI, total_log2=TOTAL_LOG2):

@@ -92,6 +92,7 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             a.sh = p->sh;
             a.spin_limit = p->spin_limit;
             a.withhold_chunk = p->withhold_chunk;
+            a.prefetch = p->pprefetch;
             e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch + (int64_t)p->pnch * p->pG), st);
             if (e == cudaSuccess)
                 e = p->ppipe ? launch_threestep_pipe(ThreeConfig{p->pl1, p->pc, p->pl2}, p->ppipe, inv, a, p->pgrid, st)

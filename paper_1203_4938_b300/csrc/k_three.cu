@@ -26,8 +26,22 @@ cudaError_t one(int op, bool inv, const ThreeArgs* a, int grid, cudaStream_t st,
         info->blocks_per_sm = nb;
         return cudaSuccess;
     }
-    if (inv) ki<<<grid, CF::THREADS, CF::SMEM, st>>>(*a);
-    else kf<<<grid, CF::THREADS, CF::SMEM, st>>>(*a);
+    // tensor maps of the L2 prefetches: the input as [batch * N1][N2] (A
+    // boxes of CA x N1), the workspace as [batch * N1 * M1][M2] (B1 boxes of
+    // CB x M1); unused (and not encoded) when a->prefetch is 0
+    CUtensorMap t_in{}, t_b1{};
+    ThreeArgs aa = *a;
+    if (aa.prefetch) {
+        const uint64_t B = (uint64_t)aa.batch, N1 = CF::N1, M1 = CF::M1, M2 = CF::M2, N2 = CF::N2;
+        const uint64_t d0[2] = {N2, B * N1}, s0[1] = {N2 * 8};
+        const uint32_t b0[2] = {(uint32_t)CF::CA, (uint32_t)N1};
+        const uint64_t d1[2] = {M2, B * N1 * M1}, s1[1] = {M2 * 8};
+        const uint32_t b1[2] = {(uint32_t)CF::CB, (uint32_t)M1};
+        if (!encode_tensor_map(&t_in, aa.in, 2, d0, s0, b0) || !encode_tensor_map(&t_b1, aa.work, 2, d1, s1, b1))
+            aa.prefetch = 0;
+    }
+    if (inv) ki<<<grid, CF::THREADS, CF::SMEM, st>>>(aa, t_in, t_b1);
+    else kf<<<grid, CF::THREADS, CF::SMEM, st>>>(aa, t_in, t_b1);
     return cudaGetLastError();
 }
 

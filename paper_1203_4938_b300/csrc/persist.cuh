@@ -91,18 +91,34 @@ k_fourstep_persist(PersistArgs a) {
     constexpr int64_t N1 = int64_t(1) << L1, N2 = int64_t(1) << L2, N = N1 * N2;
     constexpr int GA = (int)(N2 / C);    // A tiles per transform
     constexpr int GB = (int)(N1 / TPC);  // B tiles per transform
+    constexpr int T = FourStepPersistCfg<L1, C, L2, TPC>::THREADS;
+    using PA = P2Plan<L1>;
+    using PB = P2Plan<L2>;
     extern __shared__ float2 smem[];
     __shared__ int s_item[2];
     __shared__ int s_ok;
     const uint64_t pol = l2_policy_evict_last();
     const int total = a.nch * (a.na + a.nb);
+    // thread 0's bookkeeping: the next queue item (an atomic in flight) and a
+    // finished A tile's chunk counter still to be signalled; both are
+    // published only after this thread has issued its loads of the current
+    // tile, so their latency never delays them, and the signal always
+    // precedes any wait of this CTA (no deadlock)
+    int nxt = 0;
+    int pend = -1;  // chunk whose counter thread 0 still has to bump
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl, 1);
     for (int it = 0;; it ^= 1) {
         __syncthreads();  // previous tile done with smem; s_item[it] visible
         const int p = s_item[it];
         if (p >= total) break;
-        // dequeue the next item now so its latency hides behind this tile
-        if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.ctl, 1);
+        if (threadIdx.x == 0) {
+            nxt = atomicAdd(a.ctl, 1);
+            if (pend >= 0) {
+                __threadfence();
+                atomicAdd(a.ctl + 1 + pend, 1);
+                pend = -1;
+            }
+        }
         bool is_b;
         int j, r;
         decode_item(p, a.na, a.nb, a.nch, &is_b, &j, &r);
@@ -110,19 +126,27 @@ k_fourstep_persist(PersistArgs a) {
             const int64_t tr = (int64_t)j * a.cb + r / GA;
             const int g = r % GA;
             if (tr < a.batch) {
-                const int64_t off = tr * N + (int64_t)g * C;
-                cols_tile<L1, C, INV, true, Ld::Stream, St::Keep>(a.in + off, a.work + off, N2, (uint32_t)(g * C),
-                                                                  a.tw_a, a.lo, a.hi, a.sh, smem, pol);
+                const float2* src = a.in + tr * N + (int64_t)g * C + threadIdx.x % C;
+                const int t = threadIdx.x / C;
+                float2 v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = __ldcs(src + (int64_t)(t + i * PA::T) * N2);
+                if (threadIdx.x == 0) st_shared_after(&s_item[it ^ 1], nxt);
+                cols_tile_regs<L1, C, INV, true, St::Keep>(v, a.work + tr * N + (int64_t)g * C, N2,
+                                                           (uint32_t)(g * C), a.tw_a, a.lo, a.hi, a.sh, smem, pol);
+            } else if (threadIdx.x == 0) {
+                st_shared_after(&s_item[it ^ 1], nxt);
             }
-            // all stores of the tile, then one gpu-scope fence + signal (the
-            // barrier orders the other threads' stores before thread 0's fence)
-            __syncthreads();
-            if (threadIdx.x == 0 && j != a.withhold_chunk) {
-                __threadfence();
-                atomicAdd(a.ctl + 1 + j, 1);
-            }
+            // the tile's stores are ordered before the signal by the next loop
+            // barrier; thread 0 signals after its loads of the next tile
+            if (threadIdx.x == 0 && j != a.withhold_chunk) pend = j;
         } else {
             if (threadIdx.x == 0) {
+                if (pend >= 0) {  // before waiting: a pending signal may be what the wait needs
+                    __threadfence();
+                    atomicAdd(a.ctl + 1 + pend, 1);
+                    pend = -1;
+                }
                 int ok = 1;
                 int64_t spins = 0;
                 while (ld_acquire_gpu(a.ctl + 1 + j) < a.na) {
@@ -134,6 +158,7 @@ k_fourstep_persist(PersistArgs a) {
                     __nanosleep(128);
                 }
                 s_ok = ok;
+                st_shared_after(&s_item[it ^ 1], nxt);  // the atomic returned during the waits above
             }
             __syncthreads();
             const int64_t tr = (int64_t)j * a.cb + r / GB;
@@ -145,11 +170,16 @@ k_fourstep_persist(PersistArgs a) {
                 __syncthreads();
                 // the tile's workspace rows are consumed: drop them from L2
                 constexpr int LINES = (int)(TPC * N2 * 8 / 128);
-                for (int l = threadIdx.x; l < LINES; l += FourStepPersistCfg<L1, C, L2, TPC>::THREADS)
+                for (int l = threadIdx.x; l < LINES; l += T)
                     l2_discard_line(reinterpret_cast<const char*>(src) + (int64_t)l * 128);
             }
         }
     }
+    if (threadIdx.x == 0 && pend >= 0) {
+        __threadfence();
+        atomicAdd(a.ctl + 1 + pend, 1);
+    }
+    (void)PB::T;
 }
 
 }  // namespace b300fft

@@ -57,6 +57,7 @@ struct fft_plan_s {
     // persistent four-step
     int pl1 = 0, pc = 0, pl2 = 0, ptpc = 0;
     int ppipe = 0;  // > 0: the persistent four-step runs with asynchronous loads into a ring of ppipe slots
+    int pprefetch = 0;  // three-stage: L2 tensor prefetch of the next tile's box
     int pgrid = 0, pnch = 0, pna = 0, pnb = 0;
     int64_t pcb = 0;
     int64_t spin_limit = int64_t(1) << 23;

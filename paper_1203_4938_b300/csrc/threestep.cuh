@@ -27,6 +27,7 @@
 // sets FFT_ERR_TIMEOUT and skips the tile).
 #pragma once
 #include "persist.cuh"
+#include "tma.cuh"
 
 namespace b300fft {
 
@@ -51,6 +52,7 @@ struct ThreeArgs {
     int sh;
     int64_t spin_limit;
     int withhold_chunk;
+    int prefetch;  // 1: thread 0 brings the next A or B1 tile's box into L2 with one tensor prefetch
 };
 
 template <int LA, int LB1, int LB2>
@@ -135,8 +137,29 @@ __device__ __forceinline__ int three_wait(const ThreeArgs& a, const int* dep, in
 // start, a B tile waits (bounded) for its producers before loading, and a
 // producing tile is signalled (and a B2 tile's input lines dropped) right
 // after the next loop barrier -- before this CTA can wait on anything.
+// Prefetch into L2 the box the tile of queue item p will load (A: the
+// input columns, B1: the workspace columns of one row); B2 rows are left to
+// the L2 residency of the B1 output.
+template <int LA, int LB1, int LB2>
+__device__ __forceinline__ void three_prefetch(const ThreeArgs& a, int p, const CUtensorMap* t_in,
+                                               const CUtensorMap* t_b1) {
+    using CF = ThreeCfg<LA, LB1, LB2>;
+    constexpr int GA = (int)(CF::N2 / CF::CA), HB = (int)(CF::M2 / CF::CB), GPT = (int)(CF::N1 / CF::TPC);
+    int stage, c, g, r;
+    three_decode(a, p, &stage, &c, &g, &r);
+    if (stage == kStageA) {
+        const int64_t tr = (int64_t)c * a.cb + r / GA;
+        if (tr < a.batch) tma_prefetch_2d(t_in, (r % GA) * CF::CA, (int)(tr * CF::N1));
+    } else if (stage == kStageB1) {
+        const int64_t tr = (int64_t)c * a.cb + g / GPT;
+        const int64_t k1 = (int64_t)(g % GPT) * CF::TPC + r / HB;
+        if (tr < a.batch) tma_prefetch_2d(t_b1, (r % HB) * CF::CB, (int)((tr * CF::N1 + k1) * CF::M1));
+    }
+}
+
 template <int LA, int LB1, int LB2, bool INV>
-__global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
+__global__ void __launch_bounds__(256, 4)
+k_threestep(ThreeArgs a, const __grid_constant__ CUtensorMap t_in, const __grid_constant__ CUtensorMap t_b1) {
     using CF = ThreeCfg<LA, LB1, LB2>;
     constexpr int CA = CF::CA, CB = CF::CB, TPC = CF::TPC;
     constexpr int64_t N1 = CF::N1, M1 = CF::M1, M2 = CF::M2, N2 = CF::N2, N = CF::N;
@@ -148,16 +171,16 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
     __shared__ int s_item[2], s_ok;
     const uint64_t pol = l2_policy_evict_last();
     const int total = a.nch * (a.na + a.nb);
-    int* pend = nullptr;         // thread 0: counter of the previous tile, signalled after the loop barrier
+    // thread 0: the next queue item (an atomic in flight) and the counter of
+    // the previous producing tile still to be signalled (index into ctl, -1:
+    // none).  Both are published only after thread 0 has issued its loads of
+    // the current tile (or, for a tile that waits, before the wait), so their
+    // latency does not delay the tile and no CTA waits on its own signal.
+    int nxt = 0, pend = -1;
     const char* drop = nullptr;  // first input row of the previous B2 tile, dropped after the loop barrier
     if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl, 1);
     for (int it = 0;; it ^= 1) {
         __syncthreads();  // the previous tile's stores and reads are done
-        if (threadIdx.x == 0 && pend) {  // release: before any wait of this CTA
-            __threadfence();
-            atomicAdd(pend, 1);
-            pend = nullptr;
-        }
         if (drop) {
             for (int l = threadIdx.x; l < TPC * CF::RUN_LINES; l += CF::THREADS)
                 l2_discard_line(drop + (int64_t)(l / CF::RUN_LINES) * N2 * 8 + (int64_t)(l % CF::RUN_LINES) * 128);
@@ -165,7 +188,7 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
         }
         const int p = s_item[it];
         if (p >= total) break;
-        if (threadIdx.x == 0) s_item[it ^ 1] = atomicAdd(a.ctl, 1);
+        if (threadIdx.x == 0) nxt = atomicAdd(a.ctl, 1);
         int stage, c, g, r;
         three_decode(a, p, &stage, &c, &g, &r);
         if (stage == kStageA) {
@@ -177,16 +200,39 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
                 float2 v[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = __ldcs(src + (int64_t)(t + i * TA) * N2);
+                if (threadIdx.x == 0) {
+                    st_shared_after(&s_item[it ^ 1], nxt);
+                    if (a.prefetch && nxt < total) three_prefetch<LA, LB1, LB2>(a, nxt, &t_in, &t_b1);
+                    if (pend >= 0) {  // release: the previous tile's stores precede it (loop barrier)
+                        __threadfence();
+                        atomicAdd(a.ctl + pend, 1);
+                        pend = -1;
+                    }
+                }
                 cols_tile_regs<LA, CA, INV, true, St::Keep>(v, a.work + tr * N + col0, N2, col0, a.tw_a, a.lo, a.hi,
                                                             a.sh, smem, pol);
+            } else if (threadIdx.x == 0) {
+                st_shared_after(&s_item[it ^ 1], nxt);
+                if (pend >= 0) {
+                    __threadfence();
+                    atomicAdd(a.ctl + pend, 1);
+                    pend = -1;
+                }
             }
-            if (threadIdx.x == 0 && c != a.withhold_chunk) pend = a.ctl + 1 + c;
+            if (threadIdx.x == 0 && c != a.withhold_chunk) pend = 1 + c;
             continue;
         }
         if (threadIdx.x == 0) {
+            if (pend >= 0) {  // before waiting: a pending signal may be what the wait needs
+                __threadfence();
+                atomicAdd(a.ctl + pend, 1);
+                pend = -1;
+            }
             int target = 0;
             const int* dep = three_dep(a, stage, c, g, &target);
             s_ok = three_wait(a, dep, target);
+            st_shared_after(&s_item[it ^ 1], nxt);
+            if (a.prefetch && nxt < total) three_prefetch<LA, LB1, LB2>(a, nxt, &t_in, &t_b1);
         }
         __syncthreads();
         const bool ok = s_ok;
@@ -205,7 +251,7 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
                 cols_tile_regs<LB1, CB, INV, true, St::Keep>(v, base, M2, col0, a.tw_b1, a.lo, a.hi, a.sh, smem, pol,
                                                              (uint32_t)N1);
             }
-            if (threadIdx.x == 0) pend = a.ctl + 1 + a.nch + c * a.G + g;
+            if (threadIdx.x == 0) pend = 1 + a.nch + c * a.G + g;
         } else if (ok && tr < a.batch) {
             const float2* base = a.work + tr * N + k10 * N2 + (int64_t)r * M2;
             const float2* src = base + (int64_t)(threadIdx.x / TC) * N2 + (threadIdx.x & (TC - 1));
@@ -215,6 +261,10 @@ __global__ void __launch_bounds__(256, 4) k_threestep(ThreeArgs a) {
             rowsT_tile_regs<LB2, TPC, INV, St::Stream>(v, a.out + tr * N + k10 + N1 * r, N1 * M1, a.tw_b2, smem, pol);
             drop = reinterpret_cast<const char*>(base);
         }
+    }
+    if (threadIdx.x == 0 && pend >= 0) {
+        __threadfence();
+        atomicAdd(a.ctl + pend, 1);
     }
 }
 
