@@ -41,7 +41,7 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
         }
         case PlanKind::FourStepPersist: {
             if (!want(0)) break;
-            PersistArgs a;
+            PersistArgs a{};
             a.in = in;
             a.out = out;
             a.work = p->d_work;
@@ -69,7 +69,7 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
         }
         case PlanKind::ThreeStep: {
             if (!want(0)) break;
-            ThreeArgs a;
+            ThreeArgs a{};
             a.in = in;
             a.out = out;
             a.work = p->d_work;
@@ -101,7 +101,7 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
         }
         case PlanKind::TwoDPersist: {
             if (!want(0)) break;
-            PersistArgs a;
+            PersistArgs a{};
             a.in = in;
             a.out = out;
             a.work = out;
