@@ -20,6 +20,10 @@
 // tile computes, instead of every tile's warps waiting for their own global
 // loads at the start of the tile.
 //
+// Selected with B300FFT_PIPE=2|3 (or by the autotuner): on a B300 the plain
+// persistent kernel measured 10-40 % faster at every size, because the slots
+// leave room for two CTAs (18 warps) per SM instead of four.
+//
 // Ordering: a first-pass tile's stores are published by bar + fence + atomic
 // increment of the chunk counter (as in persist.cuh); the producer acquires
 // the counter and issues a proxy fence before its copies read the workspace.

@@ -16,7 +16,9 @@
 // The consumer warps (256 threads) read their 16 registers from the slot,
 // run the stage's Stockham passes with the slot as the exchange buffer and
 // store from registers, then release the slot and publish the tile (A:
-// chunk counter, B1: row-group counter).  All waits are bounded.
+// chunk counter, B1: row-group counter).  All waits are bounded.  Opt-in
+// (B300FFT_PIPE=2|3, or the autotuner's pick): the plain three-stage kernel
+// measured faster at every size on a B300.
 #pragma once
 #include "threestep.cuh"
 #include "tma.cuh"

@@ -28,6 +28,7 @@
 #include <cuda_fp16.h>
 
 #include "stockham_pow2.cuh"
+#include "tma.cuh"  // smem_u32, mbar_init
 
 namespace b300fft {
 
@@ -42,8 +43,6 @@ struct TcMode {
     static constexpr uint32_t IDESC =
         (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
     constexpr uint64_t LBO = 128, SBO = 512;
@@ -70,9 +69,6 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
