@@ -95,8 +95,9 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
             a.prefetch = p->pprefetch;
             e = cudaMemsetAsync(p->d_aux, 0, sizeof(int) * (size_t)(1 + p->pnch + (int64_t)p->pnch * p->pG), st);
             if (e == cudaSuccess)
-                e = p->ppipe ? launch_threestep_pipe(ThreeConfig{p->pl1, p->pc, p->pl2}, p->ppipe, inv, a, p->pgrid, st)
-                             : launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2}, inv, a, p->pgrid, st);
+                e = p->ppipe ? launch_threestep_pipe(ThreeConfig{p->pl1, p->pc, p->pl2, p->ptpc}, p->ppipe, inv, a,
+                                                     p->pgrid, st)
+                             : launch_threestep(ThreeConfig{p->pl1, p->pc, p->pl2, p->ptpc}, inv, a, p->pgrid, st);
             break;
         }
         case PlanKind::TwoDPersist: {

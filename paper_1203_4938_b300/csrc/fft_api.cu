@@ -107,7 +107,7 @@ fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
     static const int kCfg[25][5] = {
         {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
         {7, 32, 8, 16, 32}, {8, 16, 8, 16, 16}, {8, 16, 9, 8, 32}, {8, 16, 10, 4, 32}, {9, 16, 10, 8, 16},
-        {10, 8, 10, 8, 16}, {11, 4, 10, 8, 16}, {11, 4, 11, 4, 32}, {12, 4, 11, 8, 48}, {12, 4, 12, 4, 8}};
+        {10, 8, 10, 8, 16}, {10, 16, 11, 8, 16}, {11, 4, 11, 4, 32}, {12, 4, 11, 8, 48}, {12, 4, 12, 4, 8}};
     const Pow2Choice* force = pow2_forced();
     if (force && force->family != 2) force = nullptr;
     const bool forced = force || std::getenv("B300FFT_PERSIST_CFG") != nullptr;
@@ -186,15 +186,17 @@ fft_status build_fourstep_persist(fft_plan_s* p, int logn) {
 }
 
 // Persistent three-stage: N = N1 * M1 * M2 with 2^6 .. 2^8-point stages.
-// kThree[log2 N] = {log2 N1, log2 M1, log2 M2, chunk MiB, default on}.
+// kThree[log2 N] = {log2 N1, log2 M1, log2 M2, chunk MiB, default on, tile points}.
 // Measured on a B300 with 2^26 elements per exec: faster than the two-pass
-// persistent four-step from 2^21 on (2^19 and 2^20 are slower).  Chunks of
+// persistent four-step from 2^22 on (2^19 and 2^20 are slower, and at 2^21
+// the two-pass kernel with 16384-point tiles on 1024 threads wins: 473 vs
+// 501 us).  Chunks of
 // 32 MiB (one or two transforms): 2^21 494 us vs 503 us with 128 MiB chunks;
 // letting the A stage run more than one chunk ahead was slower at every size.
-static const int kThree[25][5] = {
+static const int kThree[25][6] = {
     {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0}, {0},
-    {6, 6, 7, 128, 0}, {6, 7, 7, 128, 0}, {7, 7, 7, 32, 1}, {7, 7, 8, 32, 1},
-    {8, 7, 8, 32, 1}, {8, 8, 8, 32, 1}};
+    {6, 6, 7, 128, 0, 4096}, {6, 7, 7, 128, 0, 4096}, {7, 7, 7, 32, 0, 4096}, {7, 7, 8, 32, 1, 4096},
+    {8, 7, 8, 32, 1, 4096}, {8, 8, 8, 32, 1, 4096}};
 
 bool three_preferred(int logn) { return logn >= 0 && logn <= 24 && kThree[logn][4] != 0; }
 
@@ -203,12 +205,13 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     if (force && force->family != 3) force = nullptr;
     const char* forced = std::getenv("B300FFT_THREE_CFG");
     if (logn > 24 || (kThree[logn][0] == 0 && !forced && !force)) return FFT_ERR_UNSUPPORTED;
-    ThreeConfig cfg{kThree[logn][0], kThree[logn][1], kThree[logn][2]};
+    ThreeConfig cfg{kThree[logn][0], kThree[logn][1], kThree[logn][2], kThree[logn][5]};
     if (forced) {
         ThreeConfig o{};
         if (std::sscanf(forced, "%d,%d,%d", &o.la, &o.lb1, &o.lb2) == 3 && o.la + o.lb1 + o.lb2 == logn) cfg = o;
     }
-    if (force) cfg = ThreeConfig{force->a, force->b, force->c};
+    cfg.tile = env_int("B300FFT_THREE_TILE", cfg.tile);
+    if (force) cfg = ThreeConfig{force->a, force->b, force->c, force->d};
     if (cfg.la + cfg.lb1 + cfg.lb2 != logn) return FFT_ERR_UNSUPPORTED;
     // asynchronous-load form (k_three_pipe.cu): ring slots, 0 = plain kernel
     // (measured slower at every size, so off by default)
@@ -228,7 +231,7 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     const int64_t n = int64_t(1) << logn;
     const int64_t n1 = int64_t(1) << cfg.la, m1 = int64_t(1) << cfg.lb1, m2 = int64_t(1) << cfg.lb2;
     const int64_t n2 = m1 * m2;
-    const int64_t ca = 4096 >> cfg.la, cb_cols = 4096 >> cfg.lb1, tpc = 4096 >> cfg.lb2;
+    const int64_t ca = cfg.tile >> cfg.la, cb_cols = cfg.tile >> cfg.lb1, tpc = cfg.tile >> cfg.lb2;
     const int64_t chunk_bytes =
         int64_t(force && force->chunk_mb ? force->chunk_mb
                                          : env_int("B300FFT_CHUNK_MB", kThree[logn][3] ? kThree[logn][3] : 32))
@@ -245,6 +248,7 @@ fft_status build_threestep(fft_plan_s* p, int logn) {
     p->pl1 = cfg.la;
     p->pc = cfg.lb1;
     p->pl2 = cfg.lb2;
+    p->ptpc = cfg.tile;
     p->pcb = cb;
     p->pnch = (int)nch;
     p->pna = (int)na;

@@ -1,6 +1,7 @@
 // k_persist.cu -- instantiations and launcher of the persistent four-step
 // kernel (persist.cuh).  Each (L1, C, L2, TPC) below is a measured or
-// candidate configuration for one log2 N.  The half-width 2^24 shape
+// candidate configuration for one log2 N (tiles of 4096, 8192 or 16384
+// points on 256, 512 or 1024 threads).  The half-width 2^24 shape
 // (12, 2, 12, 2) is deliberately absent: a build of it (with a cp.async
 // prefetch stage since removed) stopped once with an illegal instruction whose
 // cause was not found, so it is neither built nor reachable.
@@ -13,7 +14,9 @@ namespace b300fft {
     X(6, 32, 7, 16) X(7, 16, 7, 16) X(7, 32, 7, 32) X(7, 32, 8, 16)                                           \
     X(7, 16, 8, 8) X(8, 16, 8, 16) X(8, 8, 8, 8) X(8, 16, 9, 8) X(9, 8, 9, 8) X(8, 16, 10, 4) X(9, 8, 10, 4) \
         X(9, 16, 10, 8) X(10, 4, 10, 4) X(10, 8, 10, 8) X(10, 4, 11, 2) X(11, 4, 10, 8) X(11, 4, 11, 4)     \
-            X(11, 2, 11, 2) X(11, 4, 12, 2) X(12, 4, 11, 8) X(12, 4, 12, 4)
+            X(11, 2, 11, 2) X(11, 4, 12, 2) X(12, 4, 11, 8) X(12, 4, 12, 4) X(10, 8, 11, 4) X(10, 16, 11, 8)    \
+                X(11, 8, 11, 8) X(11, 8, 10, 16) X(10, 16, 10, 16) X(9, 32, 10, 16) X(9, 32, 9, 32)              \
+                    X(8, 64, 10, 16) X(8, 64, 9, 32) X(8, 64, 8, 64)
 
 namespace {
 template <int L1, int C, int L2, int TPC>

@@ -1,19 +1,23 @@
 // k_three.cu -- instantiations and launcher of the three-stage persistent
-// kernel (threestep.cuh).  Each (LA, LB1, LB2) is a candidate split of
-// log2 N into three stage lengths of 2^6 .. 2^8 points.
+// kernel (threestep.cuh).  Each (LA, LB1, LB2, TILE) is a candidate split of
+// log2 N into three stage lengths of 2^6 .. 2^8 points with a tile size.
 #include "launch.h"
 #include "threestep.cuh"
 
 namespace b300fft {
 
-#define B300_THREE_CONFIGS(X) X(6, 6, 7) X(7, 7, 6) X(6, 7, 7) X(7, 7, 7) X(7, 7, 8) X(8, 7, 8) X(7, 8, 8) X(8, 8, 8)
+// (16384-point tiles on 1024 threads compile and are exact, but measured
+// 25-30 % slower at 2^21..2^24, so none is instantiated.)
+#define B300_THREE_CONFIGS(X)                                                                          \
+    X(6, 6, 7, 4096) X(7, 7, 6, 4096) X(6, 7, 7, 4096) X(7, 7, 7, 4096) X(7, 7, 8, 4096) X(8, 7, 8, 4096) \
+        X(7, 8, 8, 4096) X(8, 8, 8, 4096)
 
 namespace {
-template <int LA, int LB1, int LB2>
+template <int LA, int LB1, int LB2, int TILE>
 cudaError_t one(int op, bool inv, const ThreeArgs* a, int grid, cudaStream_t st, PersistInfo* info) {
-    using CF = ThreeCfg<LA, LB1, LB2>;
-    auto kf = k_threestep<LA, LB1, LB2, false>;
-    auto ki = k_threestep<LA, LB1, LB2, true>;
+    using CF = ThreeCfg<LA, LB1, LB2, TILE>;
+    auto kf = k_threestep<LA, LB1, LB2, false, TILE>;
+    auto ki = k_threestep<LA, LB1, LB2, true, TILE>;
     if (op == 0) {
         cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
@@ -47,8 +51,9 @@ cudaError_t one(int op, bool inv, const ThreeArgs* a, int grid, cudaStream_t st,
 
 cudaError_t dispatch(const ThreeConfig& c, int op, bool inv, const ThreeArgs* a, int grid, cudaStream_t st,
                      PersistInfo* info) {
-#define B300_X(LA, LB1, LB2) \
-    if (c.la == LA && c.lb1 == LB1 && c.lb2 == LB2) return one<LA, LB1, LB2>(op, inv, a, grid, st, info);
+#define B300_X(LA, LB1, LB2, TILE)                                       \
+    if (c.la == LA && c.lb1 == LB1 && c.lb2 == LB2 && c.tile == TILE) \
+        return one<LA, LB1, LB2, TILE>(op, inv, a, grid, st, info);
     B300_THREE_CONFIGS(B300_X)
 #undef B300_X
     return cudaErrorInvalidValue;
@@ -56,8 +61,8 @@ cudaError_t dispatch(const ThreeConfig& c, int op, bool inv, const ThreeArgs* a,
 }  // namespace
 
 bool three_config_available(const ThreeConfig& c) {
-#define B300_X(LA, LB1, LB2) \
-    if (c.la == LA && c.lb1 == LB1 && c.lb2 == LB2) return true;
+#define B300_X(LA, LB1, LB2, TILE) \
+    if (c.la == LA && c.lb1 == LB1 && c.lb2 == LB2 && c.tile == TILE) return true;
     B300_THREE_CONFIGS(B300_X)
 #undef B300_X
     return false;

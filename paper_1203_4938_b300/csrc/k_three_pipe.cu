@@ -66,7 +66,7 @@ cudaError_t dispatch(const ThreeConfig& c, int ns, int op, bool inv, const Three
 }  // namespace
 
 bool three_pipe_available(const ThreeConfig& c, int ns) {
-    if (ns != 2 && ns != 3) return false;
+    if ((ns != 2 && ns != 3) || c.tile != 4096) return false;
 #define B300_X(LA, LB1, LB2) \
     if (c.la == LA && c.lb1 == LB1 && c.lb2 == LB2) return true;
     B300_THREE_PIPE_CONFIGS(B300_X)

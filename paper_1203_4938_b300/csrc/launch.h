@@ -133,10 +133,12 @@ cudaError_t persist2d_prepare(const PersistConfig& c, PersistInfo* info);
 cudaError_t launch_2d_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid, cudaStream_t st);
 
 // --- persistent three-stage (k_three.cu) ------------------------------------
-// N = 2^la * 2^lb1 * 2^lb2, each stage length in 2^6 .. 2^8, 4096-point tiles.
+// N = 2^la * 2^lb1 * 2^lb2, each stage length in 2^6 .. 2^8, tiles of 4096 or
+// 16384 points.
 struct ThreeArgs;  // threestep.cuh
 struct ThreeConfig {
     int la, lb1, lb2;
+    int tile = 4096;  // points per tile: 4096 (256 threads) or 16384 (1024 threads)
 };
 bool three_config_available(const ThreeConfig& c);
 cudaError_t three_prepare(const ThreeConfig& c, PersistInfo* info);

@@ -92,7 +92,7 @@ namespace b300fft {
 // autotuner times as a candidate and returns as its pick.
 struct Pow2Choice {
     int family = 0;     // 1 single-pass rows, 2 persistent four-step, 3 persistent three-stage
-    int a = 0, b = 0, c = 0, d = 0;  // four-step: l1, columns, l2, rows per tile; three-stage: la, lb1, lb2
+    int a = 0, b = 0, c = 0, d = 0;  // four-step: l1, columns, l2, rows per tile; three-stage: la, lb1, lb2, tile
     int chunk_mb = 0;   // transforms per dependency chunk, in MiB (0: table)
     int pipe = 0;       // ring slots of the asynchronous-load form (0: plain loads)
     int lookahead = 0;  // three-stage B1 lookahead in row groups (0: planner's rule)

@@ -9,10 +9,11 @@
 //   B2 (per row k1, j1):      X[k1 + N1 (j1 + M1 j2)] = sum_m2 z[k1][j1 M2 + m2] W_M2^{m2 j2}
 // (the second line is the four-step of the length-N2 transform of row k1).
 //
-// Tiles hold 4096 points and run on 256 threads (16 registers each):
-//   A  : CA = 4096 / N1 adjacent columns n2 of one transform (stride N2);
-//   B1 : CB = 4096 / M1 adjacent columns m2 of one row k1 (stride M2), in place;
-//   B2 : TPC = 4096 / M2 consecutive rows k1 at one j1 (row stride N2); the
+// Tiles hold TILE = 4096 points on 256 threads or 16384 points on 1024
+// threads (16 complex registers each):
+//   A  : CA = TILE / N1 adjacent columns n2 of one transform (stride N2);
+//   B1 : CB = TILE / M1 adjacent columns m2 of one row k1 (stride M2), in place;
+//   B2 : TPC = TILE / M2 consecutive rows k1 at one j1 (row stride N2); the
 //        output is written TPC consecutive k1 (>= 128 bytes) at a time.
 // A "group" is TPC consecutive rows k1 of one transform: its B2 tiles need
 // exactly its B1 tiles.  Queue order per chunk of transforms follows the
@@ -55,9 +56,9 @@ struct ThreeArgs {
     int prefetch;  // 1: thread 0 brings the next A or B1 tile's box into L2 with one tensor prefetch
 };
 
-template <int LA, int LB1, int LB2>
+template <int LA, int LB1, int LB2, int TILE_ = 4096>
 struct ThreeCfg {
-    static constexpr int TILE = 4096, THREADS = 256;
+    static constexpr int TILE = TILE_, THREADS = TILE_ / 16;
     static constexpr int CA = TILE >> LA, CB = TILE >> LB1, TPC = TILE >> LB2;
     static constexpr int64_t N1 = int64_t(1) << LA, M1 = int64_t(1) << LB1, M2 = int64_t(1) << LB2;
     static constexpr int64_t N2 = M1 * M2, N = N1 * N2;
@@ -65,7 +66,7 @@ struct ThreeCfg {
     static_assert(CA <= N2 && CB <= M2 && TPC <= N1, "tile wider than its matrix");
     static_assert(ColsCfg<LA, CA>::THREADS == THREADS && ColsCfg<LB1, CB>::THREADS == THREADS &&
                       RowsTCfg<LB2, TPC>::THREADS == THREADS,
-                  "all stages use 256 threads");
+                  "all stages use the same thread count");
     static constexpr int S0 = ColsCfg<LA, CA>::SMEM, S1 = ColsCfg<LB1, CB>::SMEM, S2 = RowsTCfg<LB2, TPC>::SMEM;
     static constexpr int SMEM = S0 > S1 ? (S0 > S2 ? S0 : S2) : (S1 > S2 ? S1 : S2);
     static constexpr int RUN_LINES = (int)(M2 * 8 / 128);  // 128-byte lines of one B2 input row
@@ -140,10 +141,10 @@ __device__ __forceinline__ int three_wait(const ThreeArgs& a, const int* dep, in
 // Prefetch into L2 the box the tile of queue item p will load (A: the
 // input columns, B1: the workspace columns of one row); B2 rows are left to
 // the L2 residency of the B1 output.
-template <int LA, int LB1, int LB2>
+template <int LA, int LB1, int LB2, int TILE>
 __device__ __forceinline__ void three_prefetch(const ThreeArgs& a, int p, const CUtensorMap* t_in,
                                                const CUtensorMap* t_b1) {
-    using CF = ThreeCfg<LA, LB1, LB2>;
+    using CF = ThreeCfg<LA, LB1, LB2, TILE>;
     constexpr int GA = (int)(CF::N2 / CF::CA), HB = (int)(CF::M2 / CF::CB), GPT = (int)(CF::N1 / CF::TPC);
     int stage, c, g, r;
     three_decode(a, p, &stage, &c, &g, &r);
@@ -157,10 +158,10 @@ __device__ __forceinline__ void three_prefetch(const ThreeArgs& a, int p, const 
     }
 }
 
-template <int LA, int LB1, int LB2, bool INV>
-__global__ void __launch_bounds__(256, 4)
+template <int LA, int LB1, int LB2, bool INV, int TILE = 4096>
+__global__ void __launch_bounds__(TILE / 16, 16384 / TILE)
 k_threestep(ThreeArgs a, const __grid_constant__ CUtensorMap t_in, const __grid_constant__ CUtensorMap t_b1) {
-    using CF = ThreeCfg<LA, LB1, LB2>;
+    using CF = ThreeCfg<LA, LB1, LB2, TILE>;
     constexpr int CA = CF::CA, CB = CF::CB, TPC = CF::TPC;
     constexpr int64_t N1 = CF::N1, M1 = CF::M1, M2 = CF::M2, N2 = CF::N2, N = CF::N;
     constexpr int TA = (int)(N1 / 16), TB = (int)(M1 / 16), TC = (int)(M2 / 16);  // threads per transform
@@ -202,7 +203,7 @@ k_threestep(ThreeArgs a, const __grid_constant__ CUtensorMap t_in, const __grid_
                 for (int i = 0; i < 16; ++i) v[i] = __ldcs(src + (int64_t)(t + i * TA) * N2);
                 if (threadIdx.x == 0) {
                     st_shared_after(&s_item[it ^ 1], nxt);
-                    if (a.prefetch && nxt < total) three_prefetch<LA, LB1, LB2>(a, nxt, &t_in, &t_b1);
+                    if (a.prefetch && nxt < total) three_prefetch<LA, LB1, LB2, TILE>(a, nxt, &t_in, &t_b1);
                     if (pend >= 0) {  // release: the previous tile's stores precede it (loop barrier)
                         __threadfence();
                         atomicAdd(a.ctl + pend, 1);
@@ -232,7 +233,7 @@ k_threestep(ThreeArgs a, const __grid_constant__ CUtensorMap t_in, const __grid_
             const int* dep = three_dep(a, stage, c, g, &target);
             s_ok = three_wait(a, dep, target);
             st_shared_after(&s_item[it ^ 1], nxt);
-            if (a.prefetch && nxt < total) three_prefetch<LA, LB1, LB2>(a, nxt, &t_in, &t_b1);
+            if (a.prefetch && nxt < total) three_prefetch<LA, LB1, LB2, TILE>(a, nxt, &t_in, &t_b1);
         }
         __syncthreads();
         const bool ok = s_ok;

@@ -4,7 +4,8 @@
 // has compiled for that length is a candidate: the single-pass rows kernel
 // (logn <= 14), each persistent four-step split and tile width, with plain or
 // asynchronous (tensor-memory-accelerator ring) loads and two chunk sizes,
-// and each three-stage split with plain or asynchronous loads.  A candidate
+// and each three-stage split with 4096- or 16384-point tiles, with plain or
+// asynchronous loads.  A candidate
 // is built as a real plan (the planner honours the forced choice), run twice
 // to warm up and then timed over five forward executions with CUDA events on
 // a scratch batch of the same size; the fastest wins.  Picks are cached per
@@ -83,8 +84,8 @@ std::vector<Pow2Choice> candidates(int logn) {
     for (int l1 = 6; l1 <= 12; ++l1) {
         const int l2 = logn - l1;
         if (l2 < 6 || l2 > 12) continue;
-        for (int cw = 2; cw <= 32; cw *= 2)
-            for (int tpc = 2; tpc <= 32; tpc *= 2) {
+        for (int cw = 2; cw <= 64; cw *= 2)
+            for (int tpc = 2; tpc <= 64; tpc *= 2) {
                 const PersistConfig pc{l1, cw, l2, tpc};
                 if (!persist_config_available(pc)) continue;
                 for (int mb : {16, 32}) {
@@ -115,21 +116,24 @@ std::vector<Pow2Choice> candidates(int logn) {
         for (int lb1 = 6; lb1 <= 8; ++lb1) {
             const int lb2 = logn - la - lb1;
             if (lb2 < 6 || lb2 > 8) continue;
-            const ThreeConfig tc{la, lb1, lb2};
-            if (!three_config_available(tc)) continue;
-            Pow2Choice c;
-            c.family = 3;
-            c.a = la;
-            c.b = lb1;
-            c.c = lb2;
-            c.chunk_mb = 32;
-            out.push_back(c);
-            for (int ns : {2, 3})
-                if (three_pipe_available(tc, ns)) {
-                    Pow2Choice q = c;
-                    q.pipe = ns;
-                    out.push_back(q);
-                }
+            for (int tile : {4096, 16384}) {
+                const ThreeConfig tc{la, lb1, lb2, tile};
+                if (!three_config_available(tc)) continue;
+                Pow2Choice c;
+                c.family = 3;
+                c.a = la;
+                c.b = lb1;
+                c.c = lb2;
+                c.d = tile;
+                c.chunk_mb = 32;
+                out.push_back(c);
+                for (int ns : {2, 3})
+                    if (three_pipe_available(tc, ns)) {
+                        Pow2Choice q = c;
+                        q.pipe = ns;
+                        out.push_back(q);
+                    }
+            }
         }
     return out;
 }

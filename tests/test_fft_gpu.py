@@ -170,6 +170,17 @@ def test_side_stream_and_graph_capture(torch):
     (14, {"B300FFT_SINGLE_MAX_LOG": "12"}),
     (16, {"B300FFT_PERSIST": "0"}),                              # two-launch instead of persistent
     (16, {"B300FFT_PIPE": "0"}),                                 # persistent kernel with plain loads
+    # two-pass persistent tiles of 16384 points on 1024 threads (one CTA per SM)
+    (16, {"B300FFT_PERSIST_CFG": "8,64,8,64"}),
+    (17, {"B300FFT_PERSIST_CFG": "8,64,9,32"}),
+    (18, {"B300FFT_PERSIST_CFG": "8,64,10,16", "B300FFT_CHUNK_MB": "2"}),
+    (18, {"B300FFT_PERSIST_CFG": "9,32,9,32"}),
+    (19, {"B300FFT_PERSIST_CFG": "9,32,10,16"}),
+    (20, {"B300FFT_PERSIST_CFG": "10,16,10,16", "B300FFT_CHUNK_MB": "64"}),
+    (21, {}),                                                    # 2^10 x 2^11 with 16384-point tiles (default)
+    (21, {"B300FFT_PERSIST_CFG": "11,8,10,16", "B300FFT_CHUNK_MB": "4"}),
+    (21, {"B300FFT_PERSIST_CFG": "10,8,11,4"}),
+    (22, {"B300FFT_THREE": "0", "B300FFT_PERSIST_CFG": "11,8,11,8"}),
     # persistent four-step fed by tensor-memory-accelerator copies (ring of 2 or 3 slots)
     (15, {"B300FFT_PIPE": "2"}),
     (15, {"B300FFT_PIPE": "3", "B300FFT_PERSIST_CFG": "8,16,7,32"}),

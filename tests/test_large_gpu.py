@@ -37,6 +37,7 @@ def free(torch):
 CASES_1D = [
     (1024, (TWO31 >> 10) + 3, "rows"),
     (1 << 16, (TWO31 >> 16) + 1, "fourstep-persist"),
+    (1 << 21, (TWO31 >> 21) + 1, "fourstep-persist"),  # 16384-point tiles on 1024 threads
     (1 << 24, (TWO31 >> 24) + 1, "threestep"),
     (768, TWO31 // 768 + 1, "rows-mixed"),
     (49152, TWO31 // 49152 + 1, "fourstep-mixed"),
