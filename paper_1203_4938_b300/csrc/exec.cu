@@ -14,7 +14,16 @@ fft_status exec_plan(fft_plan_s* p, const float2* in, float2* out, bool inv, cud
     auto want = [only](int k) { return only < 0 || only == k; };
     switch (p->kind) {
         case PlanKind::Rows:
-            if (want(0)) e = launch_rows(p->logn_a, inv, in, out, p->batch, p->d_tables + p->off_a, st);
+            if (!want(0)) break;
+            // (fft_exec admits only 16-byte aligned buffers, as the row copies need)
+            if (p->rows_staged && (reinterpret_cast<uintptr_t>(in) & 15) == 0)
+                // the waits are for this CTA's own copies: never shorter than ~1 s,
+                // whatever spin limit the plan was given, so a CTA never leaves
+                // with a copy into its shared memory still running
+                e = launch_rows_staged(p->logn_a, inv, in, out, p->batch, p->d_tables + p->off_a, p->d_status,
+                                       p->spin_limit > (1 << 20) ? p->spin_limit : (1 << 20), p->pgrid, st);
+            else
+                e = launch_rows(p->logn_a, inv, in, out, p->batch, p->d_tables + p->off_a, st);
             break;
         case PlanKind::FourStepMixed: {
             const int64_t n1 = int64_t(p->mix_m) << p->logn_a, n2 = int64_t(1) << p->logn_b;

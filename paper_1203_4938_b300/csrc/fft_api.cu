@@ -379,6 +379,25 @@ fft_status build_pow2_1d(fft_plan_s* p, int logn) {
         if (gen_pow2_table(p->d_tables + p->off_a, logn, 0) != cudaSuccess) return FFT_ERR_CUDA;
         if (rows_prepare(logn) != cudaSuccess) return FFT_ERR_CUDA;
         p->kernels = 1;
+        // 2^14: the persistent form with bulk-copied input staging
+        // (B300FFT_ROWS_STAGED=0|1 overrides)
+        p->rows_staged = 0;
+        const int staged = force ? force->pipe : env_int("B300FFT_ROWS_STAGED", rows_staged_default(logn));
+        PersistInfo info;
+        if (staged && rows_staged_available(logn) && rows_staged_prepare(logn, &info) == cudaSuccess &&
+            info.blocks_per_sm >= 1) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int64_t slots = (int64_t)sms * info.blocks_per_sm;
+            p->rows_staged = 1;
+            p->pgrid = (int)(p->batch < slots ? p->batch : slots);
+            p->spin_limit = env_int("B300FFT_SPIN_LIMIT", 1 << 23);
+            std::snprintf(p->desc, sizeof p->desc, "rows N=2^%d staged threads=%d grid=%d", logn, info.threads,
+                          p->pgrid);
+            return FFT_OK;
+        }
+        if (force && force->pipe) return FFT_ERR_UNSUPPORTED;
         std::snprintf(p->desc, sizeof p->desc, "rows N=2^%d tpc=%d threads=%d", logn, rows_tpc(logn),
                       rows_threads(logn));
         return FFT_OK;

@@ -9,6 +9,10 @@ namespace b300fft {
 
 // Largest power-of-two length a single CTA transforms on its own.
 constexpr int kRowsMaxLog = 14;
+// Whether plans of 2^logn use the staged persistent rows kernel by default
+// (measured per direction on 2^26 elements: 2^14 253 vs 275 us, 2^13 218 vs
+// 211 us -- two plain CTAs per SM already overlap each other's loads).
+constexpr int rows_staged_default(int logn) { return logn == 14 ? 1 : 0; }
 // Largest column length of the columns kernel.
 constexpr int kColsMaxLog = 12;
 
@@ -106,6 +110,16 @@ bool persist_config_available(const PersistConfig& c);
 cudaError_t persist_prepare(const PersistConfig& c, PersistInfo* info);
 cudaError_t launch_fourstep_persist(const PersistConfig& c, bool inv, const PersistArgs& a, int grid,
                                     cudaStream_t st);
+
+// --- persistent rows kernel with bulk-copied input staging (k_rows_staged.cu)
+// nrows contiguous transforms of 2^logn (13 or 14); `in` must be 16-byte
+// aligned (the copies read whole rows); grid <= nrows persistent CTAs; a
+// staged row that does not arrive within `polls` waits of ~1 us sets
+// *status = FFT_ERR_TIMEOUT.
+bool rows_staged_available(int logn);
+cudaError_t rows_staged_prepare(int logn, PersistInfo* info);
+cudaError_t launch_rows_staged(int logn, bool inv, const float2* in, float2* out, int64_t nrows, const float2* tw,
+                               int* status, int64_t polls, int grid, cudaStream_t st);
 
 // --- tensor maps of the asynchronous tile copies (k_pipe.cu) -----------------
 // Encode a tiled tensor map over 8-byte elements (complex64): dims[0] is the

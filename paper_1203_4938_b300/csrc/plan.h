@@ -50,6 +50,7 @@ struct fft_plan_s {
     int mix_m = 0;  // RowsMixed: L = mix_m * 2^logn_a
     int mix_mh = 0, mix_mw = 0;  // TwoDMixed: odd factor of H / W (0: power of two, logn_b / logn_a = log2)
     bool real_fused = false;     // Real: one-pass fused rows + split kernel (h = 2^5 .. 2^12)
+    int rows_staged = 0;  // Rows: persistent form with bulk-copied input staging (grid pgrid)
     int cols_c = 0;     // columns kernel width
     int rowsT_tpc = 0;  // transposed-rows kernel rows per CTA (TwoDTranspose: of the rows pass, 0: plan + transpose)
     int colsT_tpc = 0;  // TwoDTranspose: transposed-rows kernel rows per CTA of the columns pass (0: plan + transpose)
@@ -94,7 +95,7 @@ struct Pow2Choice {
     int family = 0;     // 1 single-pass rows, 2 persistent four-step, 3 persistent three-stage
     int a = 0, b = 0, c = 0, d = 0;  // four-step: l1, columns, l2, rows per tile; three-stage: la, lb1, lb2, tile
     int chunk_mb = 0;   // transforms per dependency chunk, in MiB (0: table)
-    int pipe = 0;       // ring slots of the asynchronous-load form (0: plain loads)
+    int pipe = 0;       // ring slots of the asynchronous-load form (0: plain loads); rows: 1 = staged input
     int lookahead = 0;  // three-stage B1 lookahead in row groups (0: planner's rule)
 };
 // The calling thread's forced choice (null: tables and environment decide).

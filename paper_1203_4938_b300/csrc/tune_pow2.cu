@@ -2,7 +2,8 @@
 //
 // For one length 2^logn and batch, every kernel family and shape the library
 // has compiled for that length is a candidate: the single-pass rows kernel
-// (logn <= 14), each persistent four-step split and tile width, with plain or
+// (logn <= 14; at 2^13 / 2^14 also its persistent form with staged input),
+// each persistent four-step split and tile width, with plain or
 // asynchronous (tensor-memory-accelerator ring) loads and two chunk sizes,
 // and each three-stage split with 4096- or 16384-point tiles, with plain or
 // asynchronous loads.  A candidate
@@ -80,6 +81,10 @@ std::vector<Pow2Choice> candidates(int logn) {
         Pow2Choice c;
         c.family = 1;
         out.push_back(c);
+        if (rows_staged_available(logn)) {
+            c.pipe = 1;  // persistent, bulk-copied input staging
+            out.push_back(c);
+        }
     }
     for (int l1 = 6; l1 <= 12; ++l1) {
         const int l2 = logn - l1;

@@ -50,6 +50,24 @@ def test_fourstep_large(torch, logn):
     assert max_rel_l2(y, ref, -1) <= TOL_FP32
 
 
+@pytest.mark.parametrize("staged", ["0", "1"])
+@pytest.mark.parametrize("logn", [13, 14])
+@pytest.mark.parametrize("batch", [1, 7, 300])
+def test_rows_staged_and_plain(torch, monkeypatch, staged, logn, batch):
+    """2^13 / 2^14 rows, both the plain one-CTA-per-transform kernel and the
+    persistent form that bulk-copies the next row into shared memory (batch
+    300 > grid: every CTA runs several staged rows, some one more than
+    others)."""
+    monkeypatch.setenv("B300FFT_ROWS_STAGED", staged)
+    n = 1 << logn
+    x = inputs.normal_batch(batch, n, seed=logn * 7 + batch)
+    for d in (-1, +1):
+        y = run((n,), batch, x, d)
+        assert max_rel_l2(y, oracle.fft(x, d), -1) <= TOL_FP32, (logn, batch, staged, d)
+    y = run((n,), batch, x, -1, inplace=True)
+    assert max_rel_l2(y, oracle.fft(x, -1), -1) <= TOL_FP32, (logn, batch, staged, "in place")
+
+
 def test_config_small_uniform_1024x64(torch):
     """N=1024, batch 64, uniform[-1,1] from seed 0, forward."""
     x = inputs.uniform_batch(64, 1024, seed=0)
