@@ -46,8 +46,9 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     return v;
 }
 
-// Position p of the queue -> (is_b, chunk, tile).
-__device__ __forceinline__ void decode_item(int p, int na, int nb, int nch, bool* is_b, int* chunk, int* tile) {
+// Position p of the queue -> (is_b, chunk, tile).  Host-callable too, so the
+// queue order can be checked without a GPU.
+__host__ __device__ __forceinline__ void decode_item(int p, int na, int nb, int nch, bool* is_b, int* chunk, int* tile) {
     if (p < na) {
         *is_b = false;
         *chunk = 0;

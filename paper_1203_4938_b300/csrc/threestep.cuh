@@ -75,7 +75,8 @@ struct ThreeCfg {
 enum : int { kStageA = 0, kStageB1 = 1, kStageB2 = 2 };
 
 // Queue position -> (stage, chunk c, group g, tile r within the stage unit).
-__device__ __forceinline__ void three_decode(const ThreeArgs& a, int p, int* stage, int* c, int* g, int* r) {
+// Host-callable too (queue-order checks without a GPU).
+__host__ __device__ __forceinline__ void three_decode(const ThreeArgs& a, int p, int* stage, int* c, int* g, int* r) {
     bool is_b;
     int rr;
     decode_item(p, a.na, a.nb, a.nch, &is_b, c, &rr);
