@@ -43,7 +43,8 @@ METRIC = "C2C FFT GFLOP/s (5N*log2N/t), fwd+inv sweep N=2^10..2^24, 2^26 complex
 # null until a new capture replaces them.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_dram_traffic.md")
 TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threestep.cuh", "tma.cuh",
-                   "kernels_launch.cuh", "k_rows.cu", "k_persist.cu", "k_three.cu", "twiddle.cu"]
+                   "rows_staged.cuh", "kernels_launch.cuh", "k_rows.cu", "k_rows_staged.cu", "k_persist.cu",
+                   "k_three.cu", "twiddle.cu"]
 
 
 def traffic_sources_sha() -> str:
