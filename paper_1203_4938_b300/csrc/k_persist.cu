@@ -16,7 +16,7 @@ namespace b300fft {
         X(9, 16, 10, 8) X(10, 4, 10, 4) X(10, 8, 10, 8) X(10, 4, 11, 2) X(11, 4, 10, 8) X(11, 4, 11, 4)     \
             X(11, 2, 11, 2) X(11, 4, 12, 2) X(12, 4, 11, 8) X(12, 4, 12, 4) X(10, 8, 11, 4) X(10, 16, 11, 8)    \
                 X(11, 8, 11, 8) X(11, 8, 10, 16) X(10, 16, 10, 16) X(9, 32, 10, 16) X(9, 32, 9, 32)              \
-                    X(8, 64, 10, 16) X(8, 64, 9, 32) X(8, 64, 8, 64)
+                    X(8, 64, 10, 16) X(8, 64, 9, 32) X(8, 64, 8, 64) X(10, 16, 12, 4) X(11, 8, 12, 4)
 
 namespace {
 template <int L1, int C, int L2, int TPC>

@@ -232,6 +232,8 @@ def test_side_stream_and_graph_capture(torch):
     (22, {"B300FFT_THREE": "0"}),                                # two-pass persistent instead
     (23, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "8,7,8"}),
     (23, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "7,8,8", "B300FFT_THREE_LOOKAHEAD": "64"}),
+    (22, {"B300FFT_THREE": "0", "B300FFT_PERSIST_CFG": "10,16,12,4"}),   # 128-byte first-pass segments
+    (23, {"B300FFT_THREE": "0", "B300FFT_PERSIST_CFG": "11,8,12,4"}),
     (24, {"B300FFT_THREE": "1", "B300FFT_THREE_CFG": "8,8,8"}),
     (24, {"B300FFT_THREE": "0"}),
 ])
