@@ -11,8 +11,10 @@ namespace b300fft {
 
 namespace {
 
+// Raise the shared-memory limits and size the persistent grids of the plan's
+// kernels.
 template <int MODE>
-cudaError_t prep_mode() {
+cudaError_t prep_mode(fft_plan_s* p) {
     cudaError_t e = cudaSuccess;
     auto set = [&](const void* f, int bytes) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -25,7 +27,30 @@ cudaError_t prep_mode() {
     set((const void*)k_tc_cols256<MODE, true>, tc_cols_smem());
     set((const void*)k_tc_rowsT256<MODE, false>, tc_rowsT_smem());
     set((const void*)k_tc_rowsT256<MODE, true>, tc_rowsT_smem());
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // Persistent grids: SMs x the kernels' resident CTAs per SM (their launch
+    // bounds; the occupancy query reports one per SM for these kernels, and
+    // one per SM measured 1.7x slower).  B300FFT_TC_GRID overrides the CTAs
+    // per SM (0: one CTA per work unit).
+    const char* env = std::getenv("B300FFT_TC_GRID");
+    const int per_sm = env && *env ? std::atoi(env) : -1;
+    auto grid = [&](int resident) {
+        p->tc_per_sm = per_sm > 0 ? per_sm : resident;
+        return per_sm == 0 ? 0x7fffffff : sms * p->tc_per_sm;
+    };
+    if (p->logn_a == 8 || p->logn_a == 12) p->tc_grid[0] = grid(kTcRowsPerSm);
+    if (p->logn_a == 16) {
+        p->tc_grid[0] = grid(kTcColsPerSm);
+        p->tc_grid[1] = grid(kTcRowsTPerSm);
+    }
     return e;
+}
+
+inline unsigned clamp_grid(int64_t units, int slots) {
+    return (unsigned)(units < slots ? units : slots);
 }
 
 template <int MODE>
@@ -34,9 +59,9 @@ cudaError_t launch_mode(const fft_plan_s* p, const float2* in, float2* out, bool
     const float2* tabs = p->d_tables;
     auto want = [only](int k) { return only < 0 || only == k; };
     if (p->logn_a == 8 || p->logn_a == 12) {
-        if (!want(0)) return cudaSuccess;
+        if (!want(0) || p->batch <= 0) return cudaSuccess;
         if (p->logn_a == 8) {
-            const unsigned g = (unsigned)((p->batch + 15) / 16);
+            const unsigned g = clamp_grid((p->batch + 15) / 16, p->tc_grid[0]);
             if (inv)
                 k_tc_rows<8, 16, MODE, true><<<g, 256, TcRowsCfg<8, 16>::SMEM, st>>>(in, out, p->batch, tabs,
                                                                                      p->d_status, bm);
@@ -44,7 +69,7 @@ cudaError_t launch_mode(const fft_plan_s* p, const float2* in, float2* out, bool
                 k_tc_rows<8, 16, MODE, false><<<g, 256, TcRowsCfg<8, 16>::SMEM, st>>>(in, out, p->batch, tabs,
                                                                                       p->d_status, bm);
         } else {
-            const unsigned g = (unsigned)p->batch;
+            const unsigned g = clamp_grid(p->batch, p->tc_grid[0]);
             if (inv)
                 k_tc_rows<12, 1, MODE, true><<<g, 256, TcRowsCfg<12, 1>::SMEM, st>>>(in, out, p->batch, tabs,
                                                                                     p->d_status, bm);
@@ -56,25 +81,30 @@ cudaError_t launch_mode(const fft_plan_s* p, const float2* in, float2* out, bool
     }
     // 65536 = 256 (columns, stride 256) x 256 (rows, transposed store)
     const int64_t n = 65536, groups = 256 / 16;
+    if (p->batch <= 0) return cudaSuccess;
     if (want(0)) {
-        const unsigned g = (unsigned)(groups * p->batch);
+        const int64_t units = groups * p->batch;
+        const unsigned g = clamp_grid(units, p->tc_grid[0]);
         if (inv)
-            k_tc_cols256<MODE, true><<<g, 256, tc_cols_smem(), st>>>(in, p->d_work, 256, groups, n, tabs,
+            k_tc_cols256<MODE, true><<<g, 256, tc_cols_smem(), st>>>(in, p->d_work, 256, groups, n, units, tabs,
                                                                      tabs + p->off_lo, tabs + p->off_hi, p->sh,
                                                                      p->d_status, bm);
         else
-            k_tc_cols256<MODE, false><<<g, 256, tc_cols_smem(), st>>>(in, p->d_work, 256, groups, n, tabs,
+            k_tc_cols256<MODE, false><<<g, 256, tc_cols_smem(), st>>>(in, p->d_work, 256, groups, n, units, tabs,
                                                                       tabs + p->off_lo, tabs + p->off_hi, p->sh,
                                                                       p->d_status, bm);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (want(1)) {
-        const unsigned g = (unsigned)(p->batch * 256 / 16);
+        const int64_t units = p->batch * 256 / 16;
+        const unsigned g = clamp_grid(units, p->tc_grid[1]);
         if (inv)
-            k_tc_rowsT256<MODE, true><<<g, 256, tc_rowsT_smem(), st>>>(p->d_work, out, tabs, 256, p->d_status, bm);
+            k_tc_rowsT256<MODE, true><<<g, 256, tc_rowsT_smem(), st>>>(p->d_work, out, tabs, 256, units,
+                                                                      p->d_status, bm);
         else
-            k_tc_rowsT256<MODE, false><<<g, 256, tc_rowsT_smem(), st>>>(p->d_work, out, tabs, 256, p->d_status, bm);
+            k_tc_rowsT256<MODE, false><<<g, 256, tc_rowsT_smem(), st>>>(p->d_work, out, tabs, 256, units,
+                                                                       p->d_status, bm);
     }
     return cudaGetLastError();
 }
@@ -116,16 +146,17 @@ fft_status build_tc_plan(fft_plan_s* p) {
     if (cudaGetLastError() != cudaSuccess) return FFT_ERR_CUDA;
     cudaError_t e;
     switch (p->precision) {
-        case FFT_TC_FP16: e = prep_mode<TC_FP16>(); break;
-        case FFT_TC_BF16: e = prep_mode<TC_BF16>(); break;
-        case FFT_TC_FP16_PLAIN: e = prep_mode<TC_FP16_PLAIN>(); break;
-        default: e = prep_mode<TC_BF16_PLAIN>(); break;
+        case FFT_TC_FP16: e = prep_mode<TC_FP16>(p); break;
+        case FFT_TC_BF16: e = prep_mode<TC_BF16>(p); break;
+        case FFT_TC_FP16_PLAIN: e = prep_mode<TC_FP16_PLAIN>(p); break;
+        default: e = prep_mode<TC_BF16_PLAIN>(p); break;
     }
     if (e != cudaSuccess) return FFT_ERR_CUDA;
     p->kernels = logn == 16 ? 2 : 1;
     static const char* names[] = {"fp32", "fp16 hi+lo", "bf16 hi+lo", "fp16 plain", "bf16 plain"};
-    std::snprintf(p->desc, sizeof p->desc, "tensor-core radix-16 (%s) N=2^%d %s", names[p->precision], logn,
-                  logn == 16 ? "four-step 256x256" : "single CTA");
+    std::snprintf(p->desc, sizeof p->desc, "tensor-core radix-16 (%s) N=2^%d %s, persistent grid=%d (%d per SM)",
+                  names[p->precision], logn, logn == 16 ? "four-step 256x256" : "single CTA", p->tc_grid[0],
+                  p->tc_per_sm);
     return FFT_OK;
 }
 

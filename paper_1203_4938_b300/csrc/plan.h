@@ -82,6 +82,8 @@ struct fft_plan_s {
     int64_t six_n1 = 0, six_n2 = 0;       // SixStep: N = six_n1 * six_n2 (inner: N1 points, inner2: N2 points)
     bool six_cols = false;                // SixStep: N1 = 2^8 by the columns kernel (no inner, no first transpose)
     b300fft::TcPlan* tc = nullptr;
+    int tc_grid[2] = {0, 0};  // TensorCore: persistent CTAs of its (first, second) kernel
+    int tc_per_sm = 0;        // TensorCore: persistent CTAs per SM of its last kernel
 
     int kernels = 0;
     char desc[256] = {0};

@@ -69,15 +69,21 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
+// Bounded wait for the MMA completion barrier: polls without a suspend-time
+// hint (the MMAs of one pass take a few hundred cycles, far less than the
+// ~1 us a hinted poll may sleep); false after `polls` polls.
+__device__ __forceinline__ bool tc_mma_wait(uint64_t* bar, uint32_t parity, int polls) {
+    for (int i = 0; i < polls; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -146,10 +152,33 @@ __device__ __forceinline__ double dft16_embed(int n, int k, bool inv) {
     return (k < 16) ? -sn : co;
 }
 
+// Two values rounded to a packed pair of 16-bit values (element k in the low
+// half, k + 1 in the high half) and the pair of residuals x - round(x).
+template <bool BF>
+__device__ __forceinline__ uint32_t to16x2(float x0, float x1, float* r0, float* r1) {
+    if constexpr (BF) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 b = __bfloat1622float2(h);
+        *r0 = x0 - b.x;
+        *r1 = x1 - b.y;
+        return *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        const float2 b = __half22float2(h);
+        *r0 = x0 - b.x;
+        *r1 = x1 - b.y;
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
 // Radix-16 butterfly of this thread on the tensor cores.  Called by all
 // threads of the CTA together (one butterfly each); v in/out natural order.
+// Thread 0 issues the MMAs and waits (bounded) for their completion; the
+// other threads wait in the barrier after it, then read their accumulator
+// lane.  Returns false (in every thread) when the wait ran out: the results
+// are then not read and the caller stops.
 template <int MODE>
-__device__ __forceinline__ void tc_dft16(float2 (&v)[16], TcCtx& c, int ntiles) {
+__device__ __forceinline__ bool tc_dft16(float2 (&v)[16], TcCtx& c, int ntiles) {
     constexpr bool BF = TcMode<MODE>::BF16;
     constexpr bool SPLIT = TcMode<MODE>::SPLIT;
     const int row = threadIdx.x & 127, tile = threadIdx.x >> 7;
@@ -168,18 +197,15 @@ __device__ __forceinline__ void tc_dft16(float2 (&v)[16], TcCtx& c, int ntiles) 
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            uint16_t h2[2], l2[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = kb * 8 + q * 2 + u;
-                const float x = (k < 16 ? v[k].x : v[k - 16].y) * sc;
-                float back;
-                h2[u] = to16<BF>(x, &back);
-                float dummy;
-                l2[u] = SPLIT ? to16<BF>(x - back, &dummy) : (uint16_t)0;
+            const int k = kb * 8 + q * 2;  // k and k + 1 are both real or both imaginary parts
+            const float x0 = (k < 16 ? v[k].x : v[k - 16].y) * sc;
+            const float x1 = (k < 16 ? v[k + 1].x : v[k - 15].y) * sc;
+            float r0, r1;
+            hw[q] = to16x2<BF>(x0, x1, &r0, &r1);
+            if constexpr (SPLIT) {
+                float d0, d1;
+                lw[q] = to16x2<BF>(r0, r1, &d0, &d1);
             }
-            hw[q] = (uint32_t)h2[0] | ((uint32_t)h2[1] << 16);
-            lw[q] = (uint32_t)l2[0] | ((uint32_t)l2[1] << 16);
         }
         const int off = op_off(row, kb * 8);
         *reinterpret_cast<uint4*>(ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -187,6 +213,7 @@ __device__ __forceinline__ void tc_dft16(float2 (&v)[16], TcCtx& c, int ntiles) 
     }
     fence_async_smem();
     __syncthreads();
+    int late = 0;
     if (threadIdx.x == 0) {
         tc_fence_after();
         constexpr uint32_t ID = TcMode<MODE>::IDESC;
@@ -205,46 +232,57 @@ __device__ __forceinline__ void tc_dft16(float2 (&v)[16], TcCtx& c, int ntiles) 
             }
         }
         tc_commit(c.bar);
-    }
-    // bounded wait for the MMAs
-    int spins = 0;
-    while (!mbar_try_wait(c.bar, c.phase)) {
-        if (++spins > (1 << 20)) {
-            if (threadIdx.x == 0) atomicCAS(c.status, 0, 6);
-            break;
+        // bounded wait for the MMAs
+        if (!tc_mma_wait(c.bar, c.phase, 1 << 22)) {
+            late = 1;
+            atomicCAS(c.status, 0, 6);
         }
     }
+    if (__syncthreads_or(late)) return false;
     c.phase ^= 1u;
-    __syncwarp();  // the .sync.aligned TMEM load needs the whole warp converged
     tc_fence_after();
     float f[32];
     tmem_ld32(c.tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + 32u * tile, f);
     tc_fence_before();
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = make_float2(f[j] * inv_sc, f[16 + j] * inv_sc);
+    return true;
+}
+
+// The 15 twiddles of radix-16 pass P (P >= 1) for butterfly t, loaded as
+// volatile loads so they stay ahead of the barrier that follows them.
+template <class PL, int P>
+__device__ __forceinline__ void tc_tw_load(float2 (&w)[15], int t, const float2* __restrict__ tw) {
+    constexpr int Ns = PL::ns(P);
+    const float2* twp = tw + PL::twoff(P) + (t & (Ns - 1));
+#pragma unroll
+    for (int r = 1; r < 16; ++r) w[r - 1] = ldg_nc_f2(twp + (r - 1) * Ns);
 }
 
 // Stockham passes of a 16^k transform with tensor-core butterflies.  Same
-// thread layout and exchange as run_passes (R = 16, one butterfly per thread).
+// thread layout and exchange as run_passes (R = 16, one butterfly per thread);
+// each pass's twiddles are loaded before the exchange barrier ahead of it.
+// False when an MMA wait ran out (every thread; nothing further is issued).
 template <class PL, int P, bool INV, int MODE, int CS>
-__device__ __forceinline__ void tc_run_passes(float2 (&v)[16], int t, float2* s, int coff,
-                                              const float2* __restrict__ tw, TcCtx& c, int ntiles) {
+__device__ __forceinline__ bool tc_run_passes(float2 (&v)[16], int t, float2* s, int coff,
+                                              const float2* __restrict__ tw, TcCtx& c, int ntiles,
+                                              const float2 (*w)[15] = nullptr) {
     static_assert(PL::R == 16 && PL::radix(P) == 16, "tensor-core passes are radix 16");
-    constexpr int Ns = PL::ns(P);
     if constexpr (P > 0) {
-        const float2* twp = tw + PL::twoff(P);
-        const int k = t & (Ns - 1);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], __ldg(twp + (r - 1) * Ns + k));
+        for (int r = 1; r < 16; ++r) v[r] = twmul<INV>(v[r], (*w)[r - 1]);
     }
-    tc_dft16<MODE>(v, c, ntiles);
+    if (!tc_dft16<MODE>(v, c, ntiles)) return false;
     if constexpr (P + 1 < PL::NPASS) {
         pass_scatter<PL, P, CS>(v, t, s, coff);
+        float2 wn[15];
+        tc_tw_load<PL, P + 1>(wn, t, tw);
         __syncthreads();
         pass_gather<PL, CS>(v, t, s, coff);
         __syncthreads();
-        tc_run_passes<PL, P + 1, INV, MODE, CS>(v, t, s, coff, tw, c, ntiles);
+        return tc_run_passes<PL, P + 1, INV, MODE, CS>(v, t, s, coff, tw, c, ntiles, &wn);
     }
+    return true;
 }
 
 // Shared-memory carve-up of a tensor-core CTA (after the FP32 exchange area).
@@ -279,8 +317,11 @@ __device__ __forceinline__ TcCtx tc_setup(uint8_t* base, uint32_t* tmem_slot, in
     return c;
 }
 
+// Release the CTA's TMEM.  `failed`: an MMA wait ran out; thread 0 then
+// waits once more (bounded) for those MMAs before the columns are freed.
 template <int THREADS>
-__device__ __forceinline__ void tc_teardown(const TcCtx& c) {
+__device__ __forceinline__ void tc_teardown(const TcCtx& c, bool failed = false) {
+    if (failed && threadIdx.x == 0) tc_mma_wait(c.bar, c.phase, 1 << 22);
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -306,8 +347,14 @@ struct TcRowsCfg {
     static constexpr int SMEM = XBYTES + TcSmem<THREADS>::BYTES;
 };
 
+// The kernels are persistent: each CTA allocates its TMEM columns and loads
+// the DFT operands once, then takes work units (row groups, column groups)
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Resident CTAs per SM (the
+// launch-bounds minimum, which registers and shared memory both allow; 64
+// TMEM columns each):
+constexpr int kTcRowsPerSm = 3, kTcColsPerSm = 2, kTcRowsTPerSm = 3;
 template <int LOGN, int TPC, int MODE, bool INV>
-__global__ void __launch_bounds__(TcRowsCfg<LOGN, TPC>::THREADS)
+__global__ void __launch_bounds__(TcRowsCfg<LOGN, TPC>::THREADS, kTcRowsPerSm)
 k_tc_rows(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows, const float2* __restrict__ tw,
           int* status, const uint4* __restrict__ bmat) {
     using CF = TcRowsCfg<LOGN, TPC>;
@@ -319,27 +366,31 @@ k_tc_rows(const float2* __restrict__ in, float2* __restrict__ out, int64_t nrows
     TcCtx c = tc_setup<CF::THREADS>(smem_raw + CF::XBYTES, &tmem_slot, status, bmat);
     const int t = threadIdx.x & (PL::T - 1);
     const int sub = threadIdx.x / PL::T;
-    const int64_t row = (int64_t)blockIdx.x * TPC + sub;
-    const bool ok = row < nrows;
-    const float2* src = in + row * PL::N;
-    float2 v[16];
+    bool ok = true;
+    for (int64_t grp = blockIdx.x; ok && grp * TPC < nrows; grp += gridDim.x) {
+        const int64_t row = grp * TPC + sub;
+        const bool have = row < nrows;
+        const float2* src = in + row * PL::N;
+        float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = ok ? ld_stream(src + t + i * PL::T) : make_float2(0.f, 0.f);
-    tc_run_passes<PL, 0, INV, MODE, 1>(v, t, xs + sub * PL::PADDED, 0, tw, c, CF::THREADS / 128);
-    if (ok) {
-        float2* dst = out + row * PL::N;
+        for (int i = 0; i < 16; ++i) v[i] = have ? ld_stream(src + t + i * PL::T) : make_float2(0.f, 0.f);
+        ok = tc_run_passes<PL, 0, INV, MODE, 1>(v, t, xs + sub * PL::PADDED, 0, tw, c, CF::THREADS / 128);
+        if (ok && have) {
+            float2* dst = out + row * PL::N;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) st_stream(dst + t + i * PL::T, v[i]);
+            for (int i = 0; i < 16; ++i) st_stream(dst + t + i * PL::T, v[i]);
+        }
+        __syncthreads();  // the exchange area is rewritten by the next group
     }
-    tc_teardown<CF::THREADS>(c);
+    tc_teardown<CF::THREADS>(c, !ok);
 }
 
 // Four-step pass A with tensor cores: C = 16 columns of length 256, stride S,
-// output multiplied by W_{256*S}^{n2*k1}.
+// output multiplied by W_{256*S}^{n2*k1}; units = column groups of all items.
 template <int MODE, bool INV>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, kTcColsPerSm)  // ~100 registers: a 3-CTA cap spills
 k_tc_cols256(const float2* __restrict__ in, float2* __restrict__ out, int64_t S, int64_t ngroups_per_item,
-             int64_t item_stride, const float2* __restrict__ tw, const float2* __restrict__ lo,
+             int64_t item_stride, int64_t units, const float2* __restrict__ tw, const float2* __restrict__ lo,
              const float2* __restrict__ hi, int sh, int* status, const uint4* __restrict__ bmat) {
     using PL = P2Plan<8>;
     constexpr int C = 16;
@@ -348,34 +399,41 @@ k_tc_cols256(const float2* __restrict__ in, float2* __restrict__ out, int64_t S,
     __shared__ uint32_t tmem_slot;
     float2* xs = reinterpret_cast<float2*>(smem_raw);
     TcCtx c = tc_setup<256>(smem_raw + XBYTES, &tmem_slot, status, bmat);
-    const int64_t item = blockIdx.x / ngroups_per_item;
-    const int64_t g = blockIdx.x - item * ngroups_per_item;
     const int cc = threadIdx.x % C, t = threadIdx.x / C;
-    const int64_t col = g * C + cc;
-    const float2* src = in + item * item_stride + col;
-    float2 v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = ld_stream(src + (int64_t)(t + i * PL::T) * S);
     float2* steps = xs + padi(PL::N * C);
-    for (int j = threadIdx.x; j < C * PL::R; j += 256) {
-        const int c2 = j % C, ii = j / C;
-        steps[ii * C + c2] = root2(lo, hi, (uint32_t)(g * C + c2) * (uint32_t)(ii * PL::T), sh);
-    }
-    tc_run_passes<PL, 0, INV, MODE, C>(v, t, xs, cc, tw, c, 2);
-    const float2 w0 = root2(lo, hi, (uint32_t)col * (uint32_t)t, sh);
-    float2* dst = out + item * item_stride + col;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; ok && u < units; u += gridDim.x) {
+        const int64_t item = u / ngroups_per_item;
+        const int64_t g = u - item * ngroups_per_item;
+        const int64_t col = g * C + cc;
+        const float2* src = in + item * item_stride + col;
+        float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-        st_stream(dst + (int64_t)(t + i * PL::T) * S, twmul<INV>(v[i], cmul(w0, steps[i * C + cc])));
-    tc_teardown<256>(c);
+        for (int i = 0; i < 16; ++i) v[i] = ld_stream(src + (int64_t)(t + i * PL::T) * S);
+        for (int j = threadIdx.x; j < C * PL::R; j += 256) {
+            const int c2 = j % C, ii = j / C;
+            steps[ii * C + c2] = root2(lo, hi, (uint32_t)(g * C + c2) * (uint32_t)(ii * PL::T), sh);
+        }
+        ok = tc_run_passes<PL, 0, INV, MODE, C>(v, t, xs, cc, tw, c, 2);
+        if (ok) {
+            const float2 w0 = root2(lo, hi, (uint32_t)col * (uint32_t)t, sh);
+            float2* dst = out + item * item_stride + col;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                st_stream(dst + (int64_t)(t + i * PL::T) * S, twmul<INV>(v[i], cmul(w0, steps[i * C + cc])));
+        }
+        __syncthreads();  // steps and the exchange area are rewritten by the next unit
+    }
+    tc_teardown<256>(c, !ok);
 }
 
 // Four-step pass B with tensor cores: TPC = 16 rows of length 256; the last
-// pass is re-mapped row-fastest for the transposed store (like rowsT_tile).
+// pass is re-mapped row-fastest for the transposed store (like rowsT_tile);
+// units = groups of 16 rows (nrows = items * n1 rows).
 template <int MODE, bool INV>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, kTcRowsTPerSm)
 k_tc_rowsT256(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ tw, int64_t n1,
-              int* status, const uint4* __restrict__ bmat) {
+              int64_t units, int* status, const uint4* __restrict__ bmat) {
     using PL = P2Plan<8>;
     constexpr int TPC = 16;
     using CF = RowsTCfg<8, TPC>;
@@ -384,37 +442,39 @@ k_tc_rowsT256(const float2* __restrict__ in, float2* __restrict__ out, const flo
     float2* xs = reinterpret_cast<float2*>(smem_raw);
     constexpr int XBYTES = ((CF::SMEM + 127) / 128) * 128;
     TcCtx c = tc_setup<256>(smem_raw + XBYTES, &tmem_slot, status, bmat);
-    const int64_t row0 = (int64_t)blockIdx.x * TPC;
-    const int64_t item = row0 / n1;
-    const int64_t k10 = row0 - item * n1;
     const int t = threadIdx.x & (PL::T - 1);
     const int sub = threadIdx.x / PL::T;
-    const float2* s0 = in + (row0 + sub) * PL::N;
-    float2 v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = ld_stream(s0 + t + i * PL::T);
-    // pass 0 (row-major mapping), exchange
-    tc_dft16<MODE>(v, c, 2);
-    float2* sx = xs + sub * CF::PITCH;
-    pass_scatter<PL, 0, 1>(v, t, sx, 0);
-    __syncthreads();
-    // pass 1 re-mapped: row r = threadIdx % 16, butterfly t2 = threadIdx / 16
     const int r = threadIdx.x % TPC, t2 = threadIdx.x / TPC;
-    const float2* sc = xs + r * CF::PITCH;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; ok && u < units; u += gridDim.x) {
+        const int64_t row0 = u * TPC;
+        const int64_t item = row0 / n1;
+        const int64_t k10 = row0 - item * n1;
+        const float2* s0 = in + (row0 + sub) * PL::N;
+        float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = sc[padi(t2 + i * PL::T)];
-    {
-        constexpr int Ns = PL::ns(1);
-        const float2* twp = tw + PL::twoff(1);
-        const int k = t2 & (Ns - 1);
+        for (int i = 0; i < 16; ++i) v[i] = ld_stream(s0 + t + i * PL::T);
+        // pass 0 (row-major mapping), exchange
+        ok = tc_dft16<MODE>(v, c, 2);
+        if (!ok) break;
+        float2* sx = xs + sub * CF::PITCH;
+        pass_scatter<PL, 0, 1>(v, t, sx, 0);
+        // pass 1 re-mapped: row r = threadIdx % 16, butterfly t2 = threadIdx / 16
+        float2 w[15];
+        tc_tw_load<PL, 1>(w, t2, tw);
+        __syncthreads();
+        const float2* sc = xs + r * CF::PITCH;
 #pragma unroll
-        for (int q = 1; q < 16; ++q) v[q] = twmul<INV>(v[q], __ldg(twp + (q - 1) * Ns + k));
+        for (int i = 0; i < 16; ++i) v[i] = sc[padi(t2 + i * PL::T)];
+#pragma unroll
+        for (int q = 1; q < 16; ++q) v[q] = twmul<INV>(v[q], w[q - 1]);
+        ok = tc_dft16<MODE>(v, c, 2);  // its first barrier also ends this unit's gathers
+        if (!ok) break;
+        float2* d0 = out + item * n1 * PL::N + k10 + r;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) st_stream(d0 + n1 * (int64_t)(t2 + i * PL::T), v[i]);
     }
-    tc_dft16<MODE>(v, c, 2);
-    float2* d0 = out + item * n1 * PL::N + k10 + r;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) st_stream(d0 + n1 * (int64_t)(t2 + i * PL::T), v[i]);
-    tc_teardown<256>(c);
+    tc_teardown<256>(c, !ok);
 }
 
 // Plan-time table of the B operands: out = [hi 2 KB][lo 2 KB] in the
