@@ -142,6 +142,12 @@ k_fourstep_persist(PersistArgs a) {
             // barrier; thread 0 signals after its loads of the next tile
             if (threadIdx.x == 0 && j != a.withhold_chunk) pend = j;
         } else {
+            // The wait stays after the loop barrier: the pending signal must
+            // cover every thread's stores of the previous tile (a barrier),
+            // and it must be published before waiting -- two CTAs that each
+            // waited while holding the first-pass signal the other needs
+            // (a tile of chunk c+1 pending, waiting on c; and vice versa)
+            // would never proceed.
             if (threadIdx.x == 0) {
                 if (pend >= 0) {  // before waiting: a pending signal may be what the wait needs
                     __threadfence();
@@ -168,8 +174,9 @@ k_fourstep_persist(PersistArgs a) {
                 const float2* src = a.work + tr * N + (int64_t)h * TPC * N2;
                 rowsT_tile<L2, TPC, INV, Ld::Cg, St::Stream>(src, a.out + tr * N + (int64_t)h * TPC, N1, a.tw_b,
                                                              smem, pol);
-                __syncthreads();
-                // the tile's workspace rows are consumed: drop them from L2
+                // the tile's workspace rows are consumed -- every thread used
+                // its loaded values before the tile's exchange barrier -- so
+                // drop them from L2
                 constexpr int LINES = (int)(TPC * N2 * 8 / 128);
                 for (int l = threadIdx.x; l < LINES; l += T)
                     l2_discard_line(reinterpret_cast<const char*>(src) + (int64_t)l * 128);
