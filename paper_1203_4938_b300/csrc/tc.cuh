@@ -69,9 +69,9 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Bounded wait for the MMA completion barrier: polls without a suspend-time
-// hint (the MMAs of one pass take a few hundred cycles, far less than the
-// ~1 us a hinted poll may sleep); false after `polls` polls.
+// Bounded wait for the MMA completion barrier: plain polls without a
+// suspend-time hint (the MMAs of one pass take a few hundred cycles); false
+// after `polls` polls.
 __device__ __forceinline__ bool tc_mma_wait(uint64_t* bar, uint32_t parity, int polls) {
     for (int i = 0; i < polls; ++i) {
         uint32_t ok;
