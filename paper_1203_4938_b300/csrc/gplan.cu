@@ -230,6 +230,29 @@ int lines_per_tile(int L, int want) {
     return want > 0 ? std::min(want, cap) : cap;
 }
 
+// Second-pass length of N = M * 2^k > 4096 (M = 3, 5, 7) as the batched
+// mixed four-step chooses it (build_mixed_fourstep): short mixed columns of
+// M * 2^a (a = 2 below 2^12, else k - 8, at most 6) by the compile-time
+// column tile, then rows of 2^b = 2^(k-a) <= 4096.  Measured against the
+// balanced split on uniform batches of 2^24 elements run by this executor.
+// 0 when N is not such a length.
+int64_t mixed_split_n2(int64_t n) {
+    for (int m : {3, 5, 7}) {
+        if (n % m) continue;
+        const int64_t q = n / m;
+        if (q & (q - 1)) continue;
+        int k = 0;
+        while ((int64_t(1) << k) < q) ++k;
+        if (n <= 4096) return 0;
+        int a = k >= 12 ? k - 8 : 2;
+        if (a > 6) a = 6;
+        if (k - a > 12) a = k - 12;
+        const int b = k - a;
+        return b >= 6 && b <= 12 ? int64_t(1) << b : 0;
+    }
+    return 0;
+}
+
 // Choose N = N1 * N2 (both <= tile max) for a smooth N; N2 a power of two
 // when possible (radix-16 rows, long transposed-store runs).
 bool split_four(int64_t n, int tile_max, int want_n2, int64_t* n1, int64_t* n2) {
@@ -318,7 +341,8 @@ bool build_kind(Builder& B, int64_t n, int64_t lines, const GLenConfig& cfg, int
         *w1 = n;
     } else if (is_smooth(n)) {
         int64_t n1, n2;
-        if (!split_four(n, cfg.tile_max, cfg.split_n2, &n1, &n2)) return false;
+        const int64_t want = cfg.split_n2 ? cfg.split_n2 : (env_i("B300FFT_G_MIXSPLIT", 1) ? mixed_split_n2(n) : 0);
+        if (!split_four(n, cfg.tile_max, (int)want, &n1, &n2)) return false;
         const int sa = B.shape((int)n1), sb = B.shape((int)n2);
         if (sa < 0 || sb < 0) return false;
         int shs;
@@ -595,7 +619,14 @@ std::vector<GLenConfig> tune_candidates(int64_t n, const GLenConfig& base) {
             splits.push_back({std::fabs(std::log((double)(n / b)) - std::log((double)b)), b});
         }
         std::sort(splits.begin(), splits.end());
-        for (size_t si = 0; si < splits.size() && si < 3; ++si) {
+        if (splits.size() > 3) splits.resize(3);
+        // and the batched mixed four-step's split for M * 2^k
+        const int64_t ms = mixed_split_n2(n);
+        if (ms && std::none_of(splits.begin(), splits.end(), [&](const std::pair<double, int64_t>& v) {
+                return v.second == ms;
+            }))
+            splits.insert(splits.begin(), {0.0, ms});  // first: the candidate list is capped
+        for (size_t si = 0; si < splits.size(); ++si) {
             const int64_t n2 = splits[si].second, n1 = n / n2;
             for (int la : halves(lines_per_tile((int)n1, 0)))
                 for (int lb : halves(lines_per_tile((int)n2, 0))) {
