@@ -127,13 +127,16 @@ def test_ragged_pow2_templated_stages(torch, monkeypatch, env):
             assert _ragged_check(torch, lengths, data, per_size, d, full_limit=70000) <= TOL_FP32, (env, per_size, d)
 
 
-@pytest.mark.parametrize("env", [{}, {"B300FFT_G_MIXT": "0"}])
+@pytest.mark.parametrize("env", [{}, {"B300FFT_G_MIXSPLIT": "0"}, {"B300FFT_G_MIXT": "0"}])
 def test_ragged_mixed_fourstep_transposed_rows(torch, monkeypatch, env):
-    """M * 2^k four-steps whose second stage has 64 or 128 points and a row
+    """M * 2^k four-steps in the stage graph.  Default: the batched mixed
+    four-step's split (6144 = 12 x 512, 20480 = 80 x 256, ...: short mixed
+    columns, long power-of-two rows).  With the balanced split
+    (B300FFT_G_MIXSPLIT=0) the second stage has 64 or 128 points and a row
     count the fixed 256-thread tile does not divide (5120 = 80 x 64, 6144 =
     96 x 64, 7168 = 112 x 64, 10240 = 80 x 128, ...): the compile-time
-    transposed-row tile with a partial last tile (or runtime tiles when the
-    compile-time tiles are off).  Every transform compared in full."""
+    transposed-row tile with a partial last tile; with the compile-time tiles
+    off, runtime tiles.  Every transform compared in full."""
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     lengths = [5120, 6144, 7168, 10240, 14336, 6144, 100, 4099, 20480, 3 * 2 ** 15]

@@ -48,6 +48,20 @@ def test_precision_workload_against_oracle(torch, n, batch):
         assert err <= tol, (mode, n, err)
 
 
+@pytest.mark.parametrize("grid", ["0", "1", "5"])
+@pytest.mark.parametrize("n,batch", [(256, 700), (4096, 500), (65536, 40)])
+def test_tc_persistent_grids(torch, monkeypatch, grid, n, batch):
+    """The persistent tensor-core kernels with one CTA per work unit (0), one
+    CTA per SM (1: every CTA runs many units) and more CTAs than fit at once
+    (5 per SM: the later ones start as others finish)."""
+    monkeypatch.setenv("B300FFT_TC_GRID", grid)
+    x = inputs.normal_batch(batch, n, seed=n % 1000 + batch)
+    sample = [0, 1, batch // 2, batch - 1]
+    y = run((n,), batch, x, -1, precision="tc_fp16")
+    err = max_rel_l2(y[sample], oracle.fft(x[sample], -1), -1)
+    assert err <= TOL["tc_fp16"], (grid, n, err)
+
+
 @pytest.mark.parametrize("mode", ["tc_fp16", "tc_bf16"])
 def test_tc_dynamic_range(torch, mode):
     """Per-butterfly power-of-two scaling: a large constant offset (DC of
