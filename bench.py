@@ -47,13 +47,50 @@ TRAFFIC_SOURCES = ["butterfly.cuh", "stockham_pow2.cuh", "persist.cuh", "threest
                    "k_three.cu", "twiddle.cu"]
 
 
-def traffic_sources_sha() -> str:
+def _code_only(src: str) -> str:
+    """C/CUDA source without comments and with whitespace runs collapsed, so
+    that editing a comment does not invalidate a capture of the same code."""
+    out, i, n, quote = [], 0, len(src), None
+    while i < n:
+        c = src[i]
+        if quote:
+            out.append(c)
+            if c == "\\" and i + 1 < n:
+                out.append(src[i + 1])
+                i += 2
+                continue
+            if c == quote:
+                quote = None
+            i += 1
+        elif c in "\"'":
+            quote = c
+            out.append(c)
+            i += 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(" ".join(ln.split()) for ln in "".join(out).splitlines() if ln.strip())
+
+
+def traffic_sources_sha(read=None) -> str:
+    """Hash of the code (comments ignored) of the kernels the traffic table
+    was captured from; `read(name)` returns a source's text (default: the
+    working tree)."""
     import hashlib
+    if read is None:
+        def read(f):
+            with open(os.path.join(ROOT, "paper_1203_4938_b300", "csrc", f), encoding="utf-8") as fh:
+                return fh.read()
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         h.update(f.encode())
-        with open(os.path.join(ROOT, "paper_1203_4938_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        h.update(_code_only(read(f)).encode())
     return h.hexdigest()[:16]
 
 

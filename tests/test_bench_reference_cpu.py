@@ -37,3 +37,22 @@ def test_reference_budget_bounds_the_run():
     sizes = I.sweep_sizes(bench.TOTAL_LOG2, bench.LO, bench.HI)
     large = [t for t in sizes if t[1] > (1 << 17)]
     assert len(large) == 7
+
+
+def test_traffic_hash_follows_code_not_comments():
+    """The DRAM-traffic table stays valid across comment edits of the kernel
+    sources and is invalidated by any code change."""
+    import bench
+    base = {f: "// header\nint f(int x) { /* twice */ return 2 * x; }  // done\nconst char* s = \"a // b\";\n"
+            for f in bench.TRAFFIC_SOURCES}
+    h0 = bench.traffic_sources_sha(lambda f: base[f])
+    edited = dict(base)
+    first = bench.TRAFFIC_SOURCES[0]
+    edited[first] = "// new header\n\nint f(int x) {   return 2 * x; }\nconst char* s = \"a // b\";   // note\n"
+    assert bench.traffic_sources_sha(lambda f: edited[f]) == h0
+    changed = dict(base)
+    changed[first] = base[first].replace("2 * x", "3 * x")
+    assert bench.traffic_sources_sha(lambda f: changed[f]) != h0
+    inside_string = dict(base)
+    inside_string[first] = base[first].replace('"a // b"', '"a // c"')
+    assert bench.traffic_sources_sha(lambda f: inside_string[f]) != h0
